@@ -1,0 +1,348 @@
+"""Benchmark of the S3BFS level step: GTEPS and HBM roofline fraction.
+
+Default workload: R-MAT scale 22, edgefactor 16 (A/B/C/D = 0.57/0.19/0.19/0.05,
+symmetrised, self-loops and duplicates removed, int32 CSR), 64 seeded
+non-isolated sources traversed one at a time.  One step = the 64 traversals;
+``value`` = traversed edges (Graph500 count: half the degree sum of the reached
+vertices) of all steps and ranks / the slowest rank's device time.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (sequential
+FIFO BFS, one core) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import ctypes
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+METRIC = "BFS GTEPS + HBM roofline fraction at RMAT s22; served-query p50/p99 latency"
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "rmat22": dict(kind="rmat", scale=22, edgefactor=16, seed=1, sources=64, src_seed=2),
+    "rmat16": dict(kind="rmat", scale=16, edgefactor=16, seed=1, sources=64, src_seed=2),
+    "er20": dict(kind="er", n=1 << 20, m=8 << 20, seed=4, sources=64, src_seed=2),
+    "grid4096": dict(kind="grid", rows=4096, cols=4096, p=0.01, seed=3, sources=8, src_seed=3),
+}
+
+
+def make_graph(w):
+    if w["kind"] == "rmat":
+        return graphgen.rmat(w["scale"], w["edgefactor"], seed=w["seed"])
+    if w["kind"] == "er":
+        return graphgen.erdos_renyi(w["n"], w["m"], seed=w["seed"])
+    return graphgen.grid(w["rows"], w["cols"], w["p"], seed=w["seed"])
+
+
+def sources_for(w, rp, rank):
+    src = graphgen.sample_sources(rp, w["sources"], seed=w["src_seed"] + 1000 * rank)
+    if w["kind"] == "grid" and rank == 0:
+        src = np.concatenate([[0], src[:-1]]).astype(np.int32)   # the corner: maximum depth
+    return src
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("paper_2209_08764_gb300/csrc/s3bfs.cu", "paper_2209_08764_gb300/csrc/s3bfs_device.cuh"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the level-loop kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"level_loop_{workload}.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if p.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return p.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = self.proc.communicate()[0]
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(getattr(self, "out", ""))) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w):
+    """The CPU oracle as the reference arm: sequential BFS, one core."""
+    import oracle
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    rp, ci = make_graph(w)
+    srcs = sources_for(w, rp, 0)
+    orc = oracle.Oracle(rp, ci)
+    per_step = args.ref_sources
+    level = np.empty(len(rp) - 1, np.int32)
+    parent = np.empty(len(rp) - 1, np.int32)
+    edges = 0
+    t_total = 0.0
+    k = 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        e = 0
+        for j in range(per_step):
+            s = int(srcs[k % len(srcs)])
+            k += 1
+            orc.bfs(s, level, parent)
+            e += oracle.traversed_edges(rp, level)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            t_total += dt
+            edges += e
+    gteps = edges / t_total / 1e9
+    sample = f"{per_step} of the {len(srcs)} sources per step, one traversal each"
+    line = {"metric": METRIC, "value": gteps, "unit": "GTEPS", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": config_of(args.workload, w, rp, ci),
+            "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, w, rp, ci):
+    c = {"workload": name, "n": int(len(rp) - 1), "nnz": int(len(ci)), "sources": int(w["sources"])}
+    c.update({k: v for k, v in w.items() if k not in ("kind", "sources")})
+    c["l2"] = f"inputs larger than L2: CSR {(4 * (len(rp) + len(ci))) / 2**20:.0f} MiB vs L2 129 MiB" \
+        if 4 * (len(rp) + len(ci)) > L2_BYTES else "CSR smaller than L2 (no flush)"
+    c["parallelism"] = "replicas"
+    return c
+
+
+def cpu_baseline(w, rp, ci, srcs, budget_s):
+    import oracle
+    orc = oracle.Oracle(rp, ci)
+    level = np.empty(len(rp) - 1, np.int32)
+    parent = np.empty(len(rp) - 1, np.int32)
+    edges, t, k = 0, 0.0, 0
+    while k < len(srcs) and (t < budget_s or k < 1):
+        t0 = time.perf_counter()
+        orc.bfs(int(srcs[k]), level, parent)
+        t += time.perf_counter() - t0
+        edges += oracle.traversed_edges(rp, level)
+        k += 1
+    return {"value": edges / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"first {k} of the {len(srcs)} sources, one traversal each ({t:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat22")
+    ap.add_argument("--sources", type=int, default=0, help="override the number of sources")
+    ap.add_argument("--ref-sources", type=int, default=2, help="reference arm: traversals per step")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk-edges", type=int, default=0)
+    ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--work-insensitive", action="store_true")
+    ap.add_argument("--per-phase", action="store_true", help="one launch per phase instead of the persistent loop")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.sources:
+        w["sources"] = args.sources
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    from paper_2209_08764_gb300 import binding as B
+
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.load()
+
+    rp, ci = make_graph(w)
+    n, nnz = len(rp) - 1, len(ci)
+    srcs = sources_for(w, rp, rank)
+    deg = np.diff(rp.astype(np.int64))
+    stream = torch.cuda.current_stream()
+    opts = B.bfs_opts()
+    opts.chunk_edges = args.chunk_edges
+    opts.ctas = args.ctas
+    opts.work_insensitive = 1 if args.work_insensitive else 0
+    opts.persistent = -1 if args.per_phase else 0
+    g = B.bfs_create_csr(n, nnz, rp, ci, B.BFS_VALIDATE, opts, stream.cuda_stream)
+    info = B.bfs_graph_info(g)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    st = B.bfs_stats()
+
+    # traversed edges per source (Graph500 count), from the reached set of each traversal
+    def step(record):
+        out = []
+        for s in srcs:
+            B.bfs_run(g, int(s), level, parent, st)
+            if record is not None:
+                out.append((st.ms_level_step, st.ms_total, st.reached, st.edges_scanned, st.candidates,
+                            st.num_levels))
+        return out
+
+    for _ in range(args.warmup):
+        step(None)
+    # traversed-edge count of each source (the level array of the warm-up is exact)
+    teps_edges = []
+    for s in srcs:
+        B.bfs_run(g, int(s), level, parent, None)
+        teps_edges.append(int(deg[(level >= 0).cpu().numpy()].sum() // 2))
+    edges_per_step = sum(teps_edges)
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    recs = []
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            recs += step(True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    total_edges = edges_per_step * args.steps * ws
+    gteps = total_edges / (ms_max / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the persistent level loop), byte model:
+    # 8 m_r + 32 n_r + 28 C_tot per traversal (level step; init's 8 n excluded)
+    recs = np.array(recs, dtype=np.float64)
+    ms_loop = recs[:, 0]
+    bytes_loop = 8 * recs[:, 3] + 32 * recs[:, 2] + 28 * recs[:, 4]
+    achieved = bytes_loop.sum() / (ms_loop.sum() / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_level_loop", "algorithmic_bytes_per_launch": float(bytes_loop.mean()),
+                "avg_launch_ms": float(ms_loop.mean())}
+    hmean = len(ms_loop) / np.sum(ms_loop / 1e3 / np.tile(teps_edges, args.steps)) / 1e9
+
+    # end to end through the C ABI with pinned host outputs (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hl = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        hp = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        for s in srcs[:2]:
+            B.bfs_run(g, int(s), hl, hp, None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in srcs:
+            B.bfs_run(g, int(s), hl, hp, None)
+        te = time.perf_counter() - t0
+        e2e = {"value": edges_per_step / te / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
+               "d2h_bytes_per_step": int(len(srcs) * (8 * n + ctypes.sizeof(ctypes.c_int64) * 8))}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": config_of(args.workload, w, rp, ci), "roofline": roofline,
+                "clocks": clk.summary(), "gpu_launches": int(2 * len(srcs) * args.steps),
+                "harmonic_mean_gteps_level_step": float(hmean),
+                "ms_level_step_median": float(np.median(ms_loop)),
+                "levels_median": float(np.median(recs[:, 5])),
+                "ctas": info["ctas"], "warps": info["warps"]}
+        if e2e:
+            line["e2e"] = e2e
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, rp, ci, srcs, args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    B.bfs_destroy(g)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * s3bfs.h -- C ABI of the GB300 (sm_103a) S3BFS level-step library.
+ *
+ * The library computes breadth-first-search levels with the S3BFS method of
+ * Tithi, Fogel and Chowdhury, "An Optimal Level-synchronous Shared-memory
+ * Parallel BFS Algorithm with Optimal parallel Prefix-sum Algorithm and its
+ * Implications for Energy Consumption" (arXiv 2209.08764): every level
+ * gathers the frontier's degrees, prefix-sums them, splits the level's edges
+ * into (almost) equal chunks, scans neighbours writing level and parent
+ * without locks or atomic read-modify-writes, keeps each newly reached vertex
+ * once (its final owner keeps it) and compacts the next frontier with a
+ * second prefix sum (Fig. 1; Algorithm paragraph).
+ *
+ * All entry points are plain C: pointers and sizes only.  Every integer on the
+ * path is int32 (vertex ids, CSR offsets, levels).  Functions return BFS_OK
+ * (0) or a negative BFS_E_* code; bfs_strerror() turns a code into text and
+ * bfs_last_error() gives the detail of the last failure on this host thread.
+ */
+#ifndef S3BFS_H
+#define S3BFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define BFS_OK 0
+#define BFS_E_INVAL (-1)      /* bad argument: n, nnz, CSR contents, src, k, NULL pointer */
+#define BFS_E_MULTIGRAPH (-2) /* a row repeats a neighbour (the owner-as-parent dedup needs a simple graph) */
+#define BFS_E_NOMEM (-3)      /* device or pinned-host allocation failed, or the create-time memory cap */
+#define BFS_E_CUDA (-4)       /* a CUDA runtime call or kernel launch failed; see bfs_last_error() */
+#define BFS_E_TIMEOUT (-5)    /* a device-side wait (grid barrier or scan look-back) hit its limit */
+
+/* ---- bfs_create_csr flags ---------------------------------------------- */
+#define BFS_DEVICE_PTRS 1 /* row_ptr / col_idx are device pointers (else host pointers) */
+#define BFS_VALIDATE 2    /* check the CSR on the host before use (see bfs_create_csr) */
+#define BFS_DEDUP 4       /* sort every row and drop duplicate neighbours and self-loops */
+
+/* ---- bfs_opts.debug_flags (tests only) --------------------------------- */
+#define BFS_DEBUG_STALL_BARRIER 1 /* the last CTA never arrives at the first grid barrier,
+                                     so the wait runs out and bfs_run returns BFS_E_TIMEOUT */
+
+/* Tuning knobs; a zero field takes the default.  NULL = all defaults. */
+typedef struct bfs_opts {
+  int32_t chunk_edges;      /* grain: minimum edges per warp chunk.  Level l runs
+                               P_l = min(P, ceil(e_l / chunk_edges)) warps, the
+                               work-sensitive count of Fig. 1 lines 11/16 (the
+                               paper's own formula is chunk_edges = 1).  Default 256 */
+  int32_t ctas;             /* persistent grid size G (CTAs of 256 threads); 0 = every
+                               CTA that can be co-resident on the device */
+  int32_t persistent;       /* 1 (default): one cooperative launch runs all levels,
+                               separated by device grid barriers; -1: one launch per
+                               phase with a host read of the level sizes in between */
+  int32_t work_insensitive; /* 1: every warp is active at every level (chunks of
+                               ceil(e_l / P) edges), the comparison arm of the
+                               Experimental Results */
+  int32_t spin_limit_ms;    /* limit of every device-side wait; default 1000 ms */
+  int32_t debug_flags;      /* BFS_DEBUG_* (tests only); default 0 */
+} bfs_opts;
+
+/* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */
+#define BFS_LEVEL_FIELDS 5
+/* [0] n_l          frontier size (vertices at distance l)
+ * [1] e_l          edges the level scans (sum of frontier out-degrees)
+ * [2] c_l          candidates emitted by the explore step (n_{l+1} <= c_l <= e_l)
+ * [3] active_warps P_l, warps that explored this level
+ * [4] active_sms   distinct SMs hosting those warps */
+
+/* Statistics of one traversal (all optional). */
+typedef struct bfs_stats {
+  int32_t num_levels;     /* non-empty levels, = 1 + the largest distance reached */
+  int32_t active_ctas;    /* G, CTAs of the persistent grid */
+  int64_t reached;        /* vertices with level >= 0 */
+  int64_t edges_scanned;  /* sum of e_l = out-degree sum of reached vertices */
+  int64_t candidates;     /* sum of c_l */
+  float ms_level_step;    /* device time of the level loop (all levels), CUDA events */
+  float ms_total;         /* device time including initialisation */
+  int32_t *per_level;     /* in: optional host buffer of per_level_cap * BFS_LEVEL_FIELDS int32 */
+  int32_t per_level_cap;  /* in: capacity in levels; levels beyond it are counted, not recorded */
+} bfs_stats;
+
+typedef struct bfs_graph bfs_graph; /* opaque; owned by the library */
+
+/*
+ * bfs_create_csr -- take a graph and allocate everything a traversal needs.
+ *
+ * Graph: n vertices, nnz directed edges in CSR form: row_ptr[n+1] int32 with
+ * row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz; col_idx[nnz] int32 with
+ * 0 <= col_idx[e] < n.  Out-edges are explored, so a directed CSR is allowed;
+ * an undirected graph is given with both directions.  The graph must be
+ * simple within each row (no repeated neighbour): the dedup step keeps a
+ * candidate (v, u) when parent[v] still equals u after the level, which is
+ * unique per v only if u reaches v by one edge (Fig. 1 lines 19-23 with the
+ * owner id taken to be the parent vertex).  Self-loops are harmless.
+ *
+ * Ownership: the CSR is COPIED into library-owned device memory; the caller
+ * may free its arrays when this returns.  With BFS_DEVICE_PTRS the arrays are
+ * read as device pointers, otherwise as host pointers.  BFS_VALIDATE checks
+ * all the conditions above on the host (BFS_E_INVAL / BFS_E_MULTIGRAPH);
+ * BFS_DEDUP instead rewrites every row sorted, without duplicates or
+ * self-loops.  Without either flag the CSR is trusted; a repeated neighbour
+ * may then make bfs_run fail with BFS_E_MULTIGRAPH.
+ *
+ * Work memory (all device, allocated here once): level and parent arrays
+ * (n each), two frontier records of n+1 entries x 3 int32, candidate pairs
+ * for up to nnz edges, per-warp scan state and the per-level statistics.
+ * Limits: 1 <= n < 2^31 - 8, 0 <= nnz < 2^31 - 64.
+ *
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).  All work of
+ * this graph is ordered on it.  The current CUDA device at this call is the
+ * graph's device.  Returns BFS_OK and *out, or an error code and *out = NULL.
+ */
+int bfs_create_csr(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col_idx, int flags,
+                   const bfs_opts *opts, void *cuda_stream, bfs_graph **out);
+
+/*
+ * bfs_run -- one traversal from src (Parallel-BFS(s, P), Fig. 1).
+ *
+ * level_out[n] receives hop distances (level[src] = 0, -1 = unreachable, the
+ * paper's infinity).  parent_out[n] (nullable) receives a BFS tree:
+ * parent[src] = src, -1 where unreachable, otherwise a vertex one level up
+ * with an edge to v.  The tree is not unique; which writer wins the benign
+ * race decides it (Algorithm paragraph).  Each output may be a device pointer
+ * (written in place by the kernels) or a host pointer (copied back at the
+ * end); the kind is detected per pointer.  Blocks until the traversal is
+ * complete.  stats (nullable) receives the statistics.  Errors: BFS_E_INVAL
+ * (src out of range, NULL level_out), BFS_E_TIMEOUT, BFS_E_MULTIGRAPH,
+ * BFS_E_CUDA.  Outputs are undefined on error; the graph stays usable after
+ * BFS_E_INVAL, BFS_E_TIMEOUT and BFS_E_MULTIGRAPH.
+ */
+int bfs_run(bfs_graph *g, int32_t src, int32_t *level_out, int32_t *parent_out, bfs_stats *stats);
+
+/*
+ * bfs_run_batch -- k traversals on the same graph, one per source.
+ *
+ * levels_out[k*n] (source-major: traversal i at levels_out + i*n), and
+ * parents_out[k*n] (nullable), device or host pointers as for bfs_run.  stats
+ * (nullable) points to k records.  Same semantics and errors as k calls of
+ * bfs_run; on error the index of the failing source is in bfs_last_error().
+ */
+int bfs_run_batch(bfs_graph *g, const int32_t *srcs, int32_t k, int32_t *levels_out, int32_t *parents_out,
+                  bfs_stats *stats);
+
+/* bfs_destroy -- free everything the graph owns.  NULL is a no-op. */
+void bfs_destroy(bfs_graph *g);
+
+/* bfs_strerror -- static text for a status code. */
+const char *bfs_strerror(int code);
+
+/* bfs_last_error -- detail of the last failing call on this host thread
+ * (thread-local, valid until the next call into the library). */
+const char *bfs_last_error(void);
+
+/* bfs_graph_info -- n, nnz and the persistent grid (CTAs, warps) of a graph;
+ * any output pointer may be NULL. */
+int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, int32_t *warps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S3BFS_H */

@@ -1,0 +1,609 @@
+// S3BFS level-step library for GB300 (sm_103a): kernels and the C ABI.
+//
+// Public interface: include/s3bfs.h.  Device code of the level step:
+// s3bfs_device.cuh.  Host-side CSR checks: csr_host.cpp.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "s3bfs.h"
+#include "s3bfs_device.cuh"
+
+using namespace s3bfs;
+
+// host-side CSR helpers (csr_host.cpp)
+int s3bfs_host_check_duplicates(int32_t n, const int32_t* rp, const int32_t* ci, char* msg, size_t len);
+int s3bfs_host_dedup(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* rp_out,
+                     std::vector<int32_t>* ci_out);
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// a0 (Fig. 1 lines 1-8): level = parent = -1 except level[s] = 0, parent[s] =
+// s; F_0 = [s] with its row start and degree; clear the scan and barrier state.
+__global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int n = p.n, s = p.src;
+  const bool vec = ((reinterpret_cast<uintptr_t>(p.level) | reinterpret_cast<uintptr_t>(p.parent)) & 15) == 0;
+  if (vec) {
+    int4* L4 = reinterpret_cast<int4*>(p.level);
+    int4* P4 = reinterpret_cast<int4*>(p.parent);
+    const long long n4 = n >> 2;
+    for (long long i = tid; i < n4; i += stride) {
+      int4 lv = make_int4(-1, -1, -1, -1), pv = make_int4(-1, -1, -1, -1);
+      const long long b = i << 2;
+      if (s >= b && s < b + 4) {
+        const int o = (int)(s - b);
+        if (o == 0) { lv.x = 0; pv.x = s; }
+        if (o == 1) { lv.y = 0; pv.y = s; }
+        if (o == 2) { lv.z = 0; pv.z = s; }
+        if (o == 3) { lv.w = 0; pv.w = s; }
+      }
+      L4[i] = lv;
+      P4[i] = pv;
+    }
+    for (long long v = (n4 << 2) + tid; v < n; v += stride) {
+      p.level[v] = v == s ? 0 : -1;
+      p.parent[v] = v == s ? s : -1;
+    }
+  } else {
+    for (long long v = tid; v < n; v += stride) {
+      p.level[v] = v == s ? 0 : -1;
+      p.parent[v] = v == s ? s : -1;
+    }
+  }
+  for (long long i = tid; i < p.max_chunks; i += stride) p.status[i].word = 0ull;
+  for (long long i = tid; i < ctas; i += stride) p.bar_arrive[i] = 0;
+  if (tid == 0) {
+    const int rs = p.row_ptr[s], deg = p.row_ptr[s + 1] - rs;
+    p.F[0][0] = s;
+    p.RS[0][0] = rs;
+    p.EX[0][0] = 0;
+    p.EX[0][1] = deg;
+    DevState* st = p.st;
+    st->ctrl[0].n = 1;
+    st->ctrl[0].e = deg;
+    st->ctrl[0].c = 0;
+    st->ctrl[1].n = 0;
+    st->ctrl[1].e = 0;
+    st->ctrl[1].c = 0;
+    st->err = 0;
+    st->err_where = 0;
+    st->num_levels = 0;
+    st->bar_release = 0;
+    st->reached = st->edges = st->cands = 0;
+  }
+}
+
+// The whole level loop in one cooperative launch: explore, grid barrier,
+// compact, grid barrier, per level.  Warps beyond P_l skip the level's work
+// and wait at the barrier (parked), so a small level occupies few SMs.
+__global__ void __launch_bounds__(kThreads) k_level_loop(Params p) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const int P = gridDim.x * kWarpsPerCta;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  if (threadIdx.x == 0) p.cta_smid[blockIdx.x] = sm_id();
+  int bar = 0, l = 0;
+  long long reached = 0, edges = 0, cands = 0;
+  while (true) {
+    const int par = l & 1;
+    const int n_l = ld_relaxed(&p.st->ctrl[par].n);
+    const int e_l = ld_relaxed(&p.st->ctrl[par].e);
+    if (n_l <= 0) break;
+    if (l + 2 >= (int)kEpochMask) {
+      if (leader) set_err(p, BFS_E_INVAL, 5);
+      break;
+    }
+    int P_l, C_l;
+    level_sizing(e_l, P, p.grain, p.work_insensitive, &P_l, &C_l);
+    if (leader) {
+      reached += n_l;
+      edges += e_l;
+      record_level(p, l, n_l, e_l, P_l);
+    }
+    int cnt = 0, e_begin = 0;
+    if (gw < P_l) {
+      const long long eb = (long long)gw * C_l;
+      e_begin = (int)min(eb, (long long)e_l);
+      const int e_end = (int)min(eb + C_l, (long long)e_l);
+      if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin);
+    }
+    if (!grid_sync(p, ++bar)) break;
+    if (P_l == 0) {
+      if (gw == 0 && lane == 0) publish_empty_next(p, par);
+    } else if (gw < P_l) {
+      compact_chunk(p, l, par, gw, P_l, p.cand + e_begin, cnt);
+    }
+    if (!grid_sync(p, ++bar)) break;
+    if (leader) cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+    ++l;
+  }
+  if (leader) {
+    p.st->num_levels = l;
+    p.st->reached = reached;
+    p.st->edges = edges;
+    p.st->cands = cands;
+  }
+}
+
+// Launch-per-phase mode: the same two phases as separate launches; the host
+// reads n and e of the next level in between.
+__global__ void __launch_bounds__(kThreads) k_explore(Params p, int l, int n_l, int e_l, int P_l, int C_l) {
+  const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) record_level(p, l, n_l, e_l, P_l);
+  if (gw >= P_l) return;
+  const long long eb = (long long)gw * C_l;
+  const int e_begin = (int)min(eb, (long long)e_l);
+  const int e_end = (int)min(eb + C_l, (long long)e_l);
+  int cnt = 0;
+  if (e_begin < e_end) cnt = explore_chunk(p, l, l & 1, n_l, e_l, e_begin, e_end, p.cand + e_begin);
+  if ((threadIdx.x & (kWarp - 1)) == 0) p.cand_cnt[gw] = cnt;
+}
+
+__global__ void __launch_bounds__(kThreads) k_compact(Params p, int l, int e_l, int P_l, int C_l) {
+  const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const int par = l & 1;
+  if (P_l == 0) {
+    if (gw == 0 && (threadIdx.x & (kWarp - 1)) == 0) publish_empty_next(p, par);
+    return;
+  }
+  if (gw >= P_l) return;
+  const int e_begin = (int)min((long long)gw * C_l, (long long)e_l);
+  const int cnt = ld_relaxed(&p.cand_cnt[gw]);
+  compact_chunk(p, l, par, gw, P_l, p.cand + e_begin, cnt);
+}
+
+// CSR sanity checks that every traversal relies on (no out-of-range access):
+// row_ptr starts at 0, never decreases, ends at nnz; 0 <= col_idx < n.
+__global__ void k_check_csr(int32_t n, int32_t nnz, const int32_t* rp, const int32_t* ci, int* bad) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (tid == 0 && (rp[0] != 0 || rp[n] != nnz)) *bad = 1;
+  for (long long i = tid; i < n; i += stride)
+    if (rp[i] > rp[i + 1]) *bad = 1;
+  for (long long e = tid; e < nnz; e += stride)
+    if ((unsigned)ci[e] >= (unsigned)n) *bad = 2;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct bfs_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int32_t n = 0, nnz = 0;
+  int sms = 0;
+  int ctas = 0;   // G
+  int warps = 0;  // P
+  int grain = 256;
+  int persistent = 1;
+  int work_insensitive = 0;
+  int debug_flags = 0;
+  long long spin_ns = 1000000000ll;
+  int32_t lvl_cap = 0;
+  int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr;
+  int32_t *d_level = nullptr, *d_parent = nullptr;
+  int32_t *d_F[2] = {nullptr, nullptr}, *d_RS[2] = {nullptr, nullptr}, *d_EX[2] = {nullptr, nullptr};
+  int2* d_cand = nullptr;
+  int32_t* d_cand_cnt = nullptr;
+  ChunkStatus* d_status = nullptr;
+  int32_t *d_arrive = nullptr, *d_smid = nullptr;
+  DevState* d_st = nullptr;
+  int32_t* d_lvl = nullptr;
+  DevState* h_st = nullptr;  // pinned
+  int32_t* h_smid = nullptr; // pinned
+  int32_t* h_ctrl = nullptr; // pinned, launch-per-phase mode
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  std::vector<void*> allocs;
+};
+
+static thread_local char g_last_error[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess) return fail(BFS_E_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                     \
+  } while (0)
+
+template <class T>
+static int dalloc(bfs_graph* g, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BFS_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  g->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return BFS_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" const char* bfs_strerror(int code) {
+  switch (code) {
+    case BFS_OK: return "ok";
+    case BFS_E_INVAL: return "invalid argument";
+    case BFS_E_MULTIGRAPH: return "repeated neighbour in a CSR row (the graph must be simple)";
+    case BFS_E_NOMEM: return "out of memory";
+    case BFS_E_CUDA: return "CUDA error";
+    case BFS_E_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+extern "C" const char* bfs_last_error(void) { return g_last_error; }
+
+extern "C" void bfs_destroy(bfs_graph* g) {
+  if (!g) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (void* p : g->allocs) cudaFree(p);
+  if (g->h_st) cudaFreeHost(g->h_st);
+  if (g->h_smid) cudaFreeHost(g->h_smid);
+  if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  cudaSetDevice(cur);
+  delete g;
+}
+
+extern "C" int bfs_graph_info(const bfs_graph* g, int32_t* n, int32_t* nnz, int32_t* ctas, int32_t* warps) {
+  if (!g) return fail(BFS_E_INVAL, "graph is NULL");
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (ctas) *ctas = g->ctas;
+  if (warps) *warps = g->warps;
+  return BFS_OK;
+}
+
+static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                       int flags, const bfs_opts* opts) {
+  int rc;
+  CUDA_TRY(cudaGetDevice(&g->device));
+  CUDA_TRY(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+  int coop = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device));
+  if (opts) {
+    if (opts->chunk_edges > 0) g->grain = opts->chunk_edges;
+    if (opts->persistent < 0) g->persistent = 0;
+    g->work_insensitive = opts->work_insensitive != 0;
+    if (opts->spin_limit_ms > 0) g->spin_ns = (long long)opts->spin_limit_ms * 1000000ll;
+    g->debug_flags = opts->debug_flags;
+  }
+  if (!coop) g->persistent = 0;
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, 0));
+  if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
+  g->ctas = per_sm * g->sms;
+  if (opts && opts->ctas > 0) g->ctas = std::min(g->ctas, (int)opts->ctas);
+  g->warps = g->ctas * kWarpsPerCta;
+
+  // CSR: host data is validated / cleaned on the host, then uploaded
+  std::vector<int32_t> h_rp, h_ci;
+  const bool dev_in = (flags & BFS_DEVICE_PTRS) != 0;
+  const int32_t* rp = row_ptr;
+  const int32_t* ci = col_idx;
+  if (flags & (BFS_VALIDATE | BFS_DEDUP)) {
+    if (dev_in) {
+      h_rp.resize((size_t)n + 1);
+      CUDA_TRY(cudaMemcpy(h_rp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+      if (h_rp[n] != nnz || h_rp[0] != 0) return fail(BFS_E_INVAL, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
+      h_ci.resize((size_t)std::max(nnz, 1));
+      if (nnz) CUDA_TRY(cudaMemcpy(h_ci.data(), col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost));
+      rp = h_rp.data();
+      ci = h_ci.data();
+    }
+    if (rp[0] != 0 || rp[n] != nnz) return fail(BFS_E_INVAL, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
+    for (int32_t v = 0; v < n; ++v)
+      if (rp[v] > rp[v + 1]) return fail(BFS_E_INVAL, "row_ptr decreases at %d", v);
+    for (int32_t e = 0; e < nnz; ++e)
+      if (ci[e] < 0 || ci[e] >= n) return fail(BFS_E_INVAL, "col_idx[%d] = %d out of range", e, ci[e]);
+    if (flags & BFS_DEDUP) {
+      std::vector<int32_t> rp2, ci2;
+      if (s3bfs_host_dedup(n, rp, ci, &rp2, &ci2) != 0) return fail(BFS_E_NOMEM, "dedup: host allocation failed");
+      h_rp.swap(rp2);
+      h_ci.swap(ci2);
+      rp = h_rp.data();
+      ci = h_ci.data();
+      nnz = h_rp[n];
+    } else {
+      char msg[256];
+      if (s3bfs_host_check_duplicates(n, rp, ci, msg, sizeof(msg)) != 0) return fail(BFS_E_MULTIGRAPH, "%s", msg);
+    }
+  }
+  const bool upload_from_host = !dev_in || !h_rp.empty();
+  g->n = n;
+  g->nnz = nnz;
+  const size_t nnz_pad = ((size_t)nnz + 3) / 4 * 4 + 4;
+  if ((rc = dalloc(g, &g->d_row_ptr, (size_t)n + 1)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_col_idx, nnz_pad)) != BFS_OK) return rc;
+  const cudaMemcpyKind kind = upload_from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CUDA_TRY(cudaMemcpyAsync(g->d_row_ptr, rp, sizeof(int32_t) * ((size_t)n + 1), kind, g->stream));
+  CUDA_TRY(cudaMemsetAsync(g->d_col_idx, 0, sizeof(int32_t) * nnz_pad, g->stream));
+  if (nnz) CUDA_TRY(cudaMemcpyAsync(g->d_col_idx, ci, sizeof(int32_t) * (size_t)nnz, kind, g->stream));
+
+  // work memory
+  g->lvl_cap = (int32_t)std::min<long long>((long long)n + 1, 1 << 20);
+  const int max_chunks = g->warps;
+  if ((rc = dalloc(g, &g->d_level, (size_t)n + 4)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_parent, (size_t)n + 4)) != BFS_OK) return rc;
+  for (int b = 0; b < 2; ++b) {
+    if ((rc = dalloc(g, &g->d_F[b], (size_t)n + 4)) != BFS_OK) return rc;
+    if ((rc = dalloc(g, &g->d_RS[b], (size_t)n + 4)) != BFS_OK) return rc;
+    if ((rc = dalloc(g, &g->d_EX[b], (size_t)n + 4)) != BFS_OK) return rc;
+  }
+  if ((rc = dalloc(g, &g->d_cand, (size_t)nnz + 32)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_cand_cnt, (size_t)max_chunks)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_status, (size_t)max_chunks)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_arrive, (size_t)g->ctas)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_smid, (size_t)g->ctas)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_st, 1)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_lvl, (size_t)g->lvl_cap * kLevelFields)) != BFS_OK) return rc;
+  CUDA_TRY(cudaMemsetAsync(g->d_status, 0, sizeof(ChunkStatus) * (size_t)max_chunks, g->stream));
+  CUDA_TRY(cudaMemsetAsync(g->d_st, 0, sizeof(DevState), g->stream));
+  if (cudaHostAlloc((void**)&g->h_st, sizeof(DevState), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&g->h_smid, sizeof(int32_t) * (size_t)g->ctas, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&g->h_ctrl, sizeof(LevelCtrl) * 2 + 16, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BFS_E_NOMEM, "pinned host allocation failed");
+  }
+  for (auto& e : g->ev) CUDA_TRY(cudaEventCreate(&e));
+
+  // device-side range checks (always: they guard every later access)
+  int* d_bad = nullptr;
+  if ((rc = dalloc(g, &d_bad, 1)) != BFS_OK) return rc;
+  CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), g->stream));
+  const int cgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)std::max(n, nnz) + 255) / 256)));
+  k_check_csr<<<cgrid, 256, 0, g->stream>>>(n, nnz, g->d_row_ptr, g->d_col_idx, d_bad);
+  CUDA_TRY(cudaGetLastError());
+  int bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (bad == 1) return fail(BFS_E_INVAL, "row_ptr must start at 0, never decrease and end at nnz");
+  if (bad == 2) return fail(BFS_E_INVAL, "col_idx entry out of range [0, n)");
+  return BFS_OK;
+}
+
+extern "C" int bfs_create_csr(int32_t n, int32_t nnz, const int32_t* row_ptr, const int32_t* col_idx, int flags,
+                              const bfs_opts* opts, void* cuda_stream, bfs_graph** out) {
+  if (!out) return fail(BFS_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 0x7FFFFFFF - 8) return fail(BFS_E_INVAL, "n = %d out of range [1, 2^31-8)", n);
+  if (nnz < 0 || nnz > 0x7FFFFFFF - 64) return fail(BFS_E_INVAL, "nnz = %d out of range", nnz);
+  if (!row_ptr || (nnz > 0 && !col_idx)) return fail(BFS_E_INVAL, "NULL CSR array");
+  if (flags & ~(BFS_DEVICE_PTRS | BFS_VALIDATE | BFS_DEDUP)) return fail(BFS_E_INVAL, "unknown flags 0x%x", flags);
+  bfs_graph* g = new (std::nothrow) bfs_graph();
+  if (!g) return fail(BFS_E_NOMEM, "host allocation failed");
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  const int rc = create_impl(g, n, nnz, row_ptr, col_idx, flags, opts);
+  if (rc != BFS_OK) {
+    char keep[sizeof(g_last_error)];
+    memcpy(keep, g_last_error, sizeof(keep));
+    bfs_destroy(g);
+    memcpy(g_last_error, keep, sizeof(keep));
+    return rc;
+  }
+  *out = g;
+  return BFS_OK;
+}
+
+static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* parent) {
+  Params p;
+  memset(&p, 0, sizeof(p));
+  p.n = g->n;
+  p.nnz = g->nnz;
+  p.row_ptr = g->d_row_ptr;
+  p.col_idx = g->d_col_idx;
+  p.level = level;
+  p.parent = parent;
+  for (int b = 0; b < 2; ++b) {
+    p.F[b] = g->d_F[b];
+    p.RS[b] = g->d_RS[b];
+    p.EX[b] = g->d_EX[b];
+  }
+  p.cand = g->d_cand;
+  p.cand_cnt = g->d_cand_cnt;
+  p.status = g->d_status;
+  p.bar_arrive = g->d_arrive;
+  p.cta_smid = g->d_smid;
+  p.st = g->d_st;
+  p.lvl = g->d_lvl;
+  p.lvl_cap = g->lvl_cap;
+  p.grain = g->grain;
+  p.work_insensitive = g->work_insensitive;
+  p.src = src;
+  p.max_chunks = g->warps;
+  p.debug_flags = g->debug_flags;
+  p.spin_ns = g->spin_ns;
+  return p;
+}
+
+// Enqueue one traversal (init + level loop) on the graph's stream.
+static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
+  const int igrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n / 4 + 255) / 256)));
+  k_init<<<igrid, kThreads, 0, g->stream>>>(p, g->ctas);
+  CUDA_TRY(cudaGetLastError());
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
+  if (g->persistent) {
+    Params pc = p;
+    void* args[] = {&pc};
+    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(g->ctas), dim3(kThreads), args, 0,
+                                         g->stream));
+  } else {
+    // launch per phase; the host reads n and e of every level
+    LevelCtrl* hc = reinterpret_cast<LevelCtrl*>(g->h_ctrl);
+    int l = 0;
+    CUDA_TRY(cudaMemcpyAsync(hc, &g->d_st->ctrl[0], sizeof(LevelCtrl), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+    long long reached = 0, edges = 0, cands = 0;
+    while (hc->n > 0) {
+      const int n_l = hc->n, e_l = hc->e;
+      int P_l, C_l;
+      level_sizing(e_l, g->warps, g->grain, g->work_insensitive, &P_l, &C_l);
+      reached += n_l;
+      edges += e_l;
+      const int grid = std::max(1, (P_l + kWarpsPerCta - 1) / kWarpsPerCta);
+      k_explore<<<grid, kThreads, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+      CUDA_TRY(cudaGetLastError());
+      k_compact<<<grid, kThreads, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemcpyAsync(hc, &g->d_st->ctrl[(l + 1) & 1], sizeof(LevelCtrl), cudaMemcpyDeviceToHost,
+                               g->stream));
+      CUDA_TRY(cudaMemcpyAsync(hc + 1, &g->d_st->err, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+      CUDA_TRY(cudaStreamSynchronize(g->stream));
+      if (reinterpret_cast<int32_t*>(hc + 1)[0] != 0) break;
+      cands += hc->c;
+      ++l;
+    }
+    DevState tail;
+    memset(&tail, 0, sizeof(tail));
+    tail.num_levels = l;
+    tail.reached = reached;
+    tail.edges = edges;
+    tail.cands = cands;
+    // num_levels and totals go to the device block so both modes read back alike
+    CUDA_TRY(cudaMemcpyAsync(&g->d_st->num_levels, &tail.num_levels, sizeof(int32_t), cudaMemcpyHostToDevice,
+                             g->stream));
+    CUDA_TRY(cudaMemcpyAsync(&g->d_st->reached, &tail.reached, 3 * sizeof(long long), cudaMemcpyHostToDevice,
+                             g->stream));
+    CUDA_TRY(cudaStreamSynchronize(g->stream));
+  }
+  CUDA_TRY(cudaGetLastError());
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
+  return BFS_OK;
+}
+
+static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t src) {
+  CUDA_TRY(cudaMemcpyAsync(g->h_st, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+  if (stats && g->persistent)
+    CUDA_TRY(cudaMemcpyAsync(g->h_smid, g->d_smid, sizeof(int32_t) * (size_t)g->ctas, cudaMemcpyDeviceToHost,
+                             g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  const DevState& st = *g->h_st;
+  if (st.err != 0) {
+    if (st.err == BFS_E_TIMEOUT) return fail(BFS_E_TIMEOUT, "device wait %d ran out (src %d)", st.err_where, src);
+    if (st.err == BFS_E_MULTIGRAPH)
+      return fail(BFS_E_MULTIGRAPH, "next frontier larger than n: the graph repeats a neighbour (src %d)", src);
+    return fail(st.err, "device error %d at %d (src %d)", st.err, st.err_where, src);
+  }
+  if (!stats) return BFS_OK;
+  stats->num_levels = st.num_levels;
+  stats->active_ctas = g->persistent ? g->ctas : 0;
+  stats->reached = st.reached;
+  stats->edges_scanned = st.edges;
+  stats->candidates = st.cands;
+  stats->ms_level_step = 0.f;
+  stats->ms_total = 0.f;
+  if (timed) {
+    CUDA_TRY(cudaEventElapsedTime(&stats->ms_level_step, g->ev[1], g->ev[2]));
+    CUDA_TRY(cudaEventElapsedTime(&stats->ms_total, g->ev[0], g->ev[2]));
+  }
+  if (stats->per_level && stats->per_level_cap > 0) {
+    const int L = std::min(std::min(st.num_levels, stats->per_level_cap), g->lvl_cap);
+    if (L > 0)
+      CUDA_TRY(cudaMemcpy(stats->per_level, g->d_lvl, sizeof(int32_t) * (size_t)L * kLevelFields,
+                          cudaMemcpyDeviceToHost));
+    // active SMs: distinct SMs among the CTAs that host the level's warps
+    std::vector<int> distinct((size_t)g->ctas + 1, 0);
+    if (g->persistent) {
+      std::vector<char> seen(4096, 0);
+      int cnt = 0;
+      for (int b = 0; b < g->ctas; ++b) {
+        const int s = g->h_smid[b];
+        if (s >= 0 && s < 4096 && !seen[s]) {
+          seen[s] = 1;
+          ++cnt;
+        }
+        distinct[b + 1] = cnt;
+      }
+    }
+    for (int l = 0; l < L; ++l) {
+      int32_t* r = stats->per_level + (size_t)l * kLevelFields;
+      const int ctas = std::min(g->ctas, (r[3] + kWarpsPerCta - 1) / kWarpsPerCta);
+      r[4] = g->persistent ? distinct[ctas] : -1;
+    }
+  }
+  return BFS_OK;
+}
+
+static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* parent_out, bfs_stats* stats) {
+  const bool lvl_dev = is_device_ptr(level_out);
+  const bool par_dev = parent_out && is_device_ptr(parent_out);
+  int32_t* level = lvl_dev ? level_out : g->d_level;
+  int32_t* parent = par_dev ? parent_out : g->d_parent;
+  const Params p = make_params(g, src, level, parent);
+  const bool timed = stats != nullptr;
+  int rc = enqueue_traversal(g, p, timed);
+  if (rc != BFS_OK) return rc;
+  if (!lvl_dev)
+    CUDA_TRY(cudaMemcpyAsync(level_out, level, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
+  if (parent_out && !par_dev)
+    CUDA_TRY(cudaMemcpyAsync(parent_out, parent, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost,
+                             g->stream));
+  return finish_traversal(g, stats, timed, src);
+}
+
+extern "C" int bfs_run(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* parent_out, bfs_stats* stats) {
+  if (!g) return fail(BFS_E_INVAL, "graph is NULL");
+  if (!level_out) return fail(BFS_E_INVAL, "level_out is NULL");
+  if (src < 0 || src >= g->n) return fail(BFS_E_INVAL, "src %d out of range [0, %d)", src, g->n);
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != g->device) CUDA_TRY(cudaSetDevice(g->device));
+  const int rc = run_one(g, src, level_out, parent_out, stats);
+  if (cur != g->device) cudaSetDevice(cur);
+  return rc;
+}
+
+extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32_t* levels_out,
+                             int32_t* parents_out, bfs_stats* stats) {
+  if (!g) return fail(BFS_E_INVAL, "graph is NULL");
+  if (k < 0 || (k > 0 && (!srcs || !levels_out))) return fail(BFS_E_INVAL, "bad batch arguments (k = %d)", k);
+  for (int32_t i = 0; i < k; ++i)
+    if (srcs[i] < 0 || srcs[i] >= g->n) return fail(BFS_E_INVAL, "srcs[%d] = %d out of range", i, srcs[i]);
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != g->device) CUDA_TRY(cudaSetDevice(g->device));
+  int rc = BFS_OK;
+  for (int32_t i = 0; i < k && rc == BFS_OK; ++i) {
+    rc = run_one(g, srcs[i], levels_out + (size_t)i * g->n, parents_out ? parents_out + (size_t)i * g->n : nullptr,
+                 stats ? stats + i : nullptr);
+    if (rc != BFS_OK) {
+      char keep[sizeof(g_last_error) - 32];
+      snprintf(keep, sizeof(keep), "%s", g_last_error);
+      snprintf(g_last_error, sizeof(g_last_error), "source index %d: %s", i, keep);
+    }
+  }
+  if (cur != g->device) cudaSetDevice(cur);
+  return rc;
+}

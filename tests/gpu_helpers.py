@@ -1,0 +1,82 @@
+"""Shared helpers for the GPU parity tests (imported by tests only)."""
+import ctypes
+
+import numpy as np
+
+import oracle
+from paper_2209_08764_gb300 import binding as B
+
+
+def make_opts(**kw):
+    o = B.bfs_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Dev:
+    """A graph on the GPU through the C ABI, with torch output buffers."""
+
+    def __init__(self, rp, ci, flags=B.BFS_VALIDATE, **opts):
+        import torch
+        self.torch = torch
+        self.rp = np.ascontiguousarray(rp, np.int32)
+        self.ci = np.ascontiguousarray(ci, np.int32)
+        self.n = len(self.rp) - 1
+        self.g = B.bfs_create_csr(self.n, len(self.ci), self.rp, self.ci if len(self.ci) else None, flags,
+                                  make_opts(**opts) if opts else None, torch.cuda.current_stream().cuda_stream)
+        self.info = B.bfs_graph_info(self.g)
+        self.level = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
+
+    def run(self, src, per_level_cap=0):
+        st = B.bfs_stats()
+        buf = None
+        if per_level_cap:
+            buf = (ctypes.c_int32 * (per_level_cap * B.BFS_LEVEL_FIELDS))()
+            st.per_level = ctypes.cast(buf, ctypes.POINTER(ctypes.c_int32))
+            st.per_level_cap = per_level_cap
+        B.bfs_run(self.g, int(src), self.level, self.parent, st)
+        lv = self.level.cpu().numpy()
+        par = self.parent.cpu().numpy()
+        pl = None
+        if buf is not None:
+            L = min(st.num_levels, per_level_cap)
+            pl = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS).copy()
+        return lv, par, st, pl
+
+    def close(self):
+        B.bfs_destroy(self.g)
+        self.g = None
+
+
+def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=256):
+    """Levels bit-exact, parents a valid BFS tree, per-level statistics
+    consistent with the oracle's level profile."""
+    orc = orc or oracle.Oracle(dev.rp, dev.ci)
+    want, _ = orc.bfs(src)
+    cap = 1 << 16
+    lv, par, st, pl = dev.run(src, per_level_cap=cap if per_level else 0)
+    bad = np.nonzero(lv != want)[0]
+    assert len(bad) == 0, f"src {src}: {len(bad)} levels differ, first v={bad[0]} got {lv[bad[0]]} want {want[bad[0]]}"
+    oracle.check_bfs_tree(dev.rp, dev.ci, src, lv, par, keys=keys)
+    n_l, e_l = oracle.level_profile(dev.rp, want)
+    assert st.num_levels == len(n_l)
+    assert st.reached == int(n_l.sum())
+    assert st.edges_scanned == int(e_l.sum())
+    if per_level and pl is not None:
+        L = min(len(n_l), cap)
+        assert np.array_equal(pl[:L, 0], n_l[:L]), "per-level n_l"
+        assert np.array_equal(pl[:L, 1], e_l[:L]), "per-level e_l"
+        # candidates: at least the vertices found, at most the edges into the next level
+        nxt = np.append(n_l[1:], 0)[:L]
+        rows = np.repeat(np.arange(dev.n), np.diff(dev.rp))
+        into = (want[rows] >= 0) & (want[dev.ci] == want[rows] + 1)
+        e_next = np.bincount(want[rows][into], minlength=len(n_l))[:L]
+        assert np.all(pl[:L, 2] >= nxt) and np.all(pl[:L, 2] <= e_next), "candidates out of bounds"
+        assert st.candidates == int(pl[:, 2].sum()) or L < len(n_l)
+        P = dev.info["warps"]
+        want_P = np.where(e_l[:L] > 0, np.minimum(P, -(-e_l[:L] // grain)), 0)
+        if "wi" not in dev.__dict__:
+            assert np.array_equal(pl[:L, 3], want_P), "active warps != min(P, ceil(e_l/grain))"
+    return lv, par, st, pl

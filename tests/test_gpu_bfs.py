@@ -1,0 +1,310 @@
+"""CUDA path vs the CPU oracle, through the C ABI (GPU only).
+
+Levels must match the oracle bit for bit; parents must form a valid BFS tree
+(the tree itself depends on which writer wins the benign race); per-level
+frontier sizes and edge counts must equal the oracle's level profile; the
+number of active warps per level must be min(P, ceil(e_l / grain)).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from gpu_helpers import Dev, check_against_oracle, make_opts
+from paper_2209_08764_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2209_08764_gb300 as pkg
+    pkg.build()
+    B.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def _named_graphs():
+    g = {}
+    g["path33"] = graphgen.from_edges(33, [(i, i + 1) for i in range(32)])
+    g["cycle20"] = graphgen.from_edges(20, [(i, (i + 1) % 20) for i in range(20)])
+    g["star5000"] = graphgen.from_edges(5001, [(0, j) for j in range(1, 5001)])  # hub degree >> chunk
+    g["K40"] = graphgen.from_edges(40, list(itertools.combinations(range(40), 2)))
+    g["K7_9"] = graphgen.from_edges(16, [(i, 7 + j) for i in range(7) for j in range(9)])
+    g["grid45x77"] = graphgen.grid(45, 77, 0.0)
+    g["tree"] = graphgen.from_edges(1023, [(i, c) for i in range(1023) for c in (2 * i + 1, 2 * i + 2) if c < 1023])
+    g["two_paths"] = graphgen.from_edges(9, [(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 7), (7, 8)])
+    g["single"] = (np.array([0, 0], np.int32), np.zeros(0, np.int32))
+    g["isolated_src"] = graphgen.from_edges(4, [(1, 2), (2, 3)])
+    return g
+
+
+@pytest.mark.parametrize("name", sorted(_named_graphs()))
+def test_named_graphs(name):
+    rp, ci = _named_graphs()[name]
+    d = Dev(rp, ci)
+    try:
+        n = len(rp) - 1
+        srcs = sorted({0, n // 2, n - 1})
+        for s in srcs:
+            check_against_oracle(d, s)
+    finally:
+        d.close()
+
+
+def _directed_csr(n, edges):
+    edges = sorted(set(edges))
+    rp = np.zeros(n + 1, np.int64)
+    for u, _ in edges:
+        rp[u + 1] += 1
+    return np.cumsum(rp).astype(np.int32), np.array([v for _, v in edges], np.int32)
+
+
+def test_directed_with_zero_outdegree_frontier():
+    rng = np.random.default_rng(5)
+    n = 3000
+    e = [(int(a), int(b)) for a, b in rng.integers(0, n, size=(9000, 2)) if a != b]
+    e += [(0, v) for v in range(1, 200)]           # a hub whose neighbours mostly have out-degree 0
+    rp, ci = _directed_csr(n, e)
+    d = Dev(rp, ci)
+    try:
+        for s in (0, 1, 17, 2999):
+            check_against_oracle(d, s)
+    finally:
+        d.close()
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    rp, ci = graphgen.rmat_s16()
+    return rp, ci, graphgen.sample_sources(rp, 64, seed=2), oracle.edge_keys(rp, ci)
+
+
+def test_rmat16_64_sources(rmat16):
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci)
+    orc = oracle.Oracle(rp, ci)
+    try:
+        for s in srcs:
+            check_against_oracle(d, int(s), orc=orc, keys=keys)
+    finally:
+        d.close()
+
+
+@pytest.mark.parametrize("opts", [
+    dict(chunk_edges=1), dict(chunk_edges=2), dict(chunk_edges=3), dict(chunk_edges=31), dict(chunk_edges=32),
+    dict(chunk_edges=33), dict(chunk_edges=4096), dict(ctas=1), dict(ctas=3), dict(ctas=5, chunk_edges=7),
+    dict(persistent=-1), dict(persistent=-1, chunk_edges=5), dict(work_insensitive=1),
+    dict(work_insensitive=1, ctas=2),
+], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
+def test_rmat16_launch_configurations(rmat16, opts):
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci, **opts)
+    if opts.get("work_insensitive"):
+        d.wi = True
+    orc = oracle.Oracle(rp, ci)
+    try:
+        for s in srcs[:6]:
+            check_against_oracle(d, int(s), orc=orc, keys=keys, grain=opts.get("chunk_edges", 256))
+    finally:
+        d.close()
+
+
+def test_work_insensitive_uses_every_warp(rmat16):
+    rp, ci, srcs, _ = rmat16
+    d = Dev(rp, ci, work_insensitive=1)
+    try:
+        _, _, st, pl = d.run(int(srcs[0]), per_level_cap=64)
+        P = d.info["warps"]
+        assert np.all(pl[pl[:, 1] > 0, 3] == P)
+    finally:
+        d.close()
+
+
+def test_repeated_runs_race_stress(rmat16):
+    """The owner race is benign: 50 runs give identical levels; parents may
+    differ between runs but are always valid."""
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci, chunk_edges=3)
+    try:
+        s = int(srcs[1])
+        want, _ = oracle.bfs(rp, ci, s)
+        parents = set()
+        for _ in range(50):
+            lv, par, _, _ = d.run(s)
+            assert np.array_equal(lv, want)
+            oracle.check_bfs_tree(rp, ci, s, lv, par, keys=keys)
+            parents.add(hash(par.tobytes()))
+    finally:
+        d.close()
+
+
+def test_host_outputs_and_no_parent(rmat16):
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci)
+    try:
+        s = int(srcs[2])
+        want, _ = oracle.bfs(rp, ci, s)
+        lv = np.empty(d.n, np.int32)
+        par = np.empty(d.n, np.int32)
+        B.bfs_run(d.g, s, lv, par, None)
+        assert np.array_equal(lv, want)
+        oracle.check_bfs_tree(rp, ci, s, lv, par, keys=keys)
+        lv2 = np.full(d.n, 7, np.int32)
+        B.bfs_run(d.g, s, lv2, None, None)
+        assert np.array_equal(lv2, want)
+        d.level.fill_(5)
+        B.bfs_run(d.g, s, d.level, None, None)
+        assert np.array_equal(d.level.cpu().numpy(), want)
+    finally:
+        d.close()
+
+
+def test_unaligned_device_outputs(rmat16):
+    import torch
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci)
+    try:
+        s = int(srcs[3])
+        want, _ = oracle.bfs(rp, ci, s)
+        big = torch.empty(2 * d.n + 8, dtype=torch.int32, device="cuda")
+        lv, par = big[1:1 + d.n], big[d.n + 3:2 * d.n + 3]
+        B.bfs_run(d.g, s, lv, par, None)
+        assert np.array_equal(lv.cpu().numpy(), want)
+        oracle.check_bfs_tree(rp, ci, s, lv.cpu().numpy(), par.cpu().numpy(), keys=keys)
+    finally:
+        d.close()
+
+
+def test_run_batch_matches_single_runs(rmat16):
+    import torch
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci)
+    try:
+        k = 16
+        S = np.ascontiguousarray(srcs[:k])
+        L = torch.empty(k * d.n, dtype=torch.int32, device="cuda")
+        P = torch.empty(k * d.n, dtype=torch.int32, device="cuda")
+        B.bfs_run_batch(d.g, S, k, L, P, None)
+        L = L.cpu().numpy().reshape(k, d.n)
+        P = P.cpu().numpy().reshape(k, d.n)
+        orc = oracle.Oracle(rp, ci)
+        for i, s in enumerate(S):
+            want, _ = orc.bfs(int(s))
+            assert np.array_equal(L[i], want)
+            oracle.check_bfs_tree(rp, ci, int(s), L[i], P[i], keys=keys)
+        # host outputs, per-run stats
+        Lh = np.empty((4, d.n), np.int32)
+        st = (B.bfs_stats * 4)()
+        B.bfs_run_batch(d.g, S[:4], 4, Lh, None, st)
+        for i in range(4):
+            want, _ = orc.bfs(int(S[i]))
+            assert np.array_equal(Lh[i], want)
+            assert st[i].reached == int((want >= 0).sum())
+    finally:
+        d.close()
+
+
+def test_er_and_grid_small():
+    for rp, ci in (graphgen.erdos_renyi(1 << 14, 1 << 17, seed=4), graphgen.grid(128, 128, 0.01, seed=3)):
+        d = Dev(rp, ci)
+        orc = oracle.Oracle(rp, ci)
+        try:
+            for s in graphgen.sample_sources(rp, 4, seed=2):
+                check_against_oracle(d, int(s), orc=orc)
+            check_against_oracle(d, 0, orc=orc)
+        finally:
+            d.close()
+
+
+# ---------------------------------------------------------------------------
+# errors (all raised on the host or by a bounded device wait)
+# ---------------------------------------------------------------------------
+
+def test_bad_source_and_bad_csr():
+    rp, ci = graphgen.from_edges(10, [(i, i + 1) for i in range(9)])
+    d = Dev(rp, ci)
+    try:
+        with pytest.raises(B.BFSError) as e:
+            B.bfs_run(d.g, 10, d.level, None, None)
+        assert e.value.code == B.BFS_E_INVAL
+        with pytest.raises(B.BFSError) as e:
+            B.bfs_run(d.g, -1, d.level, None, None)
+        assert e.value.code == B.BFS_E_INVAL
+        check_against_oracle(d, 3)          # still usable
+    finally:
+        d.close()
+    bad = ci.copy()
+    bad[3] = 10
+    for flags in (0, B.BFS_VALIDATE):
+        with pytest.raises(B.BFSError) as e:
+            B.bfs_create_csr(10, len(bad), rp, bad, flags)
+        assert e.value.code == B.BFS_E_INVAL
+    rp2 = rp.copy()
+    rp2[4], rp2[5] = rp2[5], rp2[4]
+    with pytest.raises(B.BFSError) as e:
+        B.bfs_create_csr(10, len(ci), rp2, ci, 0)
+    assert e.value.code == B.BFS_E_INVAL
+    with pytest.raises(B.BFSError) as e:
+        B.bfs_create_csr(0, 0, np.zeros(1, np.int32), None, 0)
+    assert e.value.code == B.BFS_E_INVAL
+
+
+def test_multigraph_rejected_or_deduplicated():
+    rp = np.array([0, 3, 5, 6, 7], np.int32)      # row 0 lists 1 twice, row 1 has a self-loop
+    ci = np.array([1, 2, 1, 0, 1, 0, 1], np.int32)
+    with pytest.raises(B.BFSError) as e:
+        B.bfs_create_csr(4, 7, rp, ci, B.BFS_VALIDATE)
+    assert e.value.code == B.BFS_E_MULTIGRAPH
+    d = Dev(rp, ci, flags=B.BFS_DEDUP)
+    try:
+        lv, par, st, _ = d.run(0)
+        assert lv.tolist() == [0, 1, 1, -1]     # 3 -> 1 only: vertex 3 is not reachable
+        lv, par, st, _ = d.run(3)
+        assert lv.tolist() == [2, 1, 3, 0]
+    finally:
+        d.close()
+
+
+def test_device_pointer_input():
+    import torch
+    rp, ci = graphgen.rmat(12, 16, seed=3)
+    drp = torch.from_numpy(rp).cuda()
+    dci = torch.from_numpy(ci).cuda()
+    g = B.bfs_create_csr(len(rp) - 1, len(ci), drp, dci, B.BFS_DEVICE_PTRS,
+                         None, torch.cuda.current_stream().cuda_stream)
+    try:
+        del drp, dci
+        torch.cuda.synchronize()
+        lv = torch.empty(len(rp) - 1, dtype=torch.int32, device="cuda")
+        s = int(graphgen.sample_sources(rp, 1)[0])
+        B.bfs_run(g, s, lv, None, None)
+        want, _ = oracle.bfs(rp, ci, s)
+        assert np.array_equal(lv.cpu().numpy(), want)
+    finally:
+        B.bfs_destroy(g)
+
+
+def test_barrier_wait_limit_reports_timeout():
+    """A CTA that never arrives at the first grid barrier (test hook): the
+    bounded wait expires, the kernel returns, bfs_run reports BFS_E_TIMEOUT,
+    and the graph and the context stay usable."""
+    rp, ci = graphgen.rmat(10, 16, seed=1)
+    s = int(graphgen.sample_sources(rp, 1)[0])
+    d = Dev(rp, ci, debug_flags=B.BFS_DEBUG_STALL_BARRIER, spin_limit_ms=200, ctas=4)
+    try:
+        with pytest.raises(B.BFSError) as e:
+            B.bfs_run(d.g, s, d.level, d.parent, None)
+        assert e.value.code == B.BFS_E_TIMEOUT
+    finally:
+        d.close()
+    d = Dev(rp, ci)
+    try:
+        check_against_oracle(d, s)
+    finally:
+        d.close()
