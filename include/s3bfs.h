@@ -157,6 +157,41 @@ const char *bfs_last_error(void);
  * any output pointer may be NULL. */
 int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, int32_t *warps);
 
+/*
+ * bfs_run_csr_noalloc -- one traversal that allocates no memory at all.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they traverse, e.g. code running inside a
+ * host framework whose caching allocator owns the GPU's memory (a second
+ * allocator would fragment its pool or exceed its budget), or latency-critical
+ * loops where cudaMalloc / cudaFree would synchronise the device and stall
+ * other streams.  It never calls cudaMalloc, cudaFree or any allocating
+ * library routine.
+ *
+ * Arguments: a CSR as for bfs_create_csr, but as DEVICE pointers owned by the
+ * caller (row_ptr[n+1], col_idx[nnz]; read only, no alignment needed); the
+ * source; and DEVICE outputs level_out[n] and parent_out[n] (both required),
+ * with the meaning of bfs_run.  cuda_stream as for bfs_create_csr.  Blocks until
+ * the traversal is complete.
+ *
+ * Working memory: one static device array of about 32 MB that every GPU
+ * loading this library's device code reserves until the process exits.  It
+ * bounds the sizes: 1 <= n <= 262,144 and 0 <= nnz <= 2,097,152; larger graphs
+ * are rejected with BFS_E_INVAL and a message in bfs_last_error().  The CSR is
+ * range-checked on every call (BFS_E_INVAL); it must be simple within rows, as
+ * for bfs_create_csr without BFS_VALIDATE.
+ *
+ * Every call, from any thread or stream, shares that one array, which keeps
+ * the last call's contents; each call clears the state that must start at
+ * zero.  Calls that overlap on the GPU (different streams or host threads on
+ * the same device) race on the array and give wrong results: serialise them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and the grid size; make that first call before any
+ * stream capture.
+ */
+int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col_idx, int32_t src,
+                        int32_t *level_out, int32_t *parent_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

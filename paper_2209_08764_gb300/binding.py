@@ -30,7 +30,7 @@ BFS_DEBUG_STALL_BARRIER = 1
 BFS_LEVEL_FIELDS = 5
 
 EXPORTS = ("bfs_create_csr", "bfs_run", "bfs_run_batch", "bfs_destroy", "bfs_strerror", "bfs_last_error",
-           "bfs_graph_info")
+           "bfs_graph_info", "bfs_run_csr_noalloc")
 
 
 class bfs_opts(ctypes.Structure):
@@ -97,6 +97,8 @@ def load():
     lib.bfs_graph_info.restype = ctypes.c_int
     lib.bfs_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i32)]
+    lib.bfs_run_csr_noalloc.restype = ctypes.c_int
+    lib.bfs_run_csr_noalloc.argtypes = [i32, i32, i32p, i32p, i32, i32p, i32p, vp]
     _lib = lib
     return lib
 
@@ -169,3 +171,14 @@ def bfs_graph_info(g: int) -> dict:
     n, nnz, ctas, warps = (ctypes.c_int32() for _ in range(4))
     _check(load().bfs_graph_info(g, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(ctas), ctypes.byref(warps)))
     return {"n": n.value, "nnz": nnz.value, "ctas": ctas.value, "warps": warps.value}
+
+
+def bfs_run_csr_noalloc(n: int, nnz: int, row_ptr, col_idx, src: int, level_out, parent_out,
+                        cuda_stream: int | None = None) -> None:
+    """One traversal with no allocation: device CSR and device outputs from the
+    caller, working memory in the library's fixed static device array (for
+    callers that must not allocate device memory; sizes are capped)."""
+    rc = load().bfs_run_csr_noalloc(int(n), int(nnz), _addr(row_ptr, "row_ptr"), _addr(col_idx, "col_idx"),
+                                    int(src), _addr(level_out, "level_out"), _addr(parent_out, "parent_out"),
+                                    cuda_stream or None)
+    _check(rc)

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -600,10 +601,158 @@ extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32
                  stats ? stats + i : nullptr);
     if (rc != BFS_OK) {
       char keep[sizeof(g_last_error) - 32];
-      snprintf(keep, sizeof(keep), "%s", g_last_error);
+      snprintf(keep, sizeof(keep), "%.*s", (int)sizeof(keep) - 1, g_last_error);
       snprintf(g_last_error, sizeof(g_last_error), "source index %d: %s", i, keep);
     }
   }
   if (cur != g->device) cudaSetDevice(cur);
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// bfs_run_csr_noalloc: one traversal that allocates nothing
+// ---------------------------------------------------------------------------
+//
+// For callers that cannot allocate device memory while they traverse: code
+// embedded in a host framework whose caching allocator owns the GPU's memory
+// (a second allocator would fragment its pool or push it over its budget),
+// and latency-critical loops where cudaMalloc / cudaFree would synchronise the
+// device and stall other streams.  The caller passes the CSR and the outputs;
+// all working memory sits in one file-scope device array of fixed maximum
+// size, which every GPU that loads this library's device code reserves until
+// the process exits.  Maximum: kNoAllocMaxN vertices, kNoAllocMaxNnz edges.
+
+constexpr int kNoAllocMaxN = 1 << 18;     // 262,144 vertices
+constexpr int kNoAllocMaxNnz = 1 << 21;   // 2,097,152 directed edges
+constexpr int kNoAllocMaxCtas = 2048;     // cap of the persistent grid
+constexpr int kNoAllocMaxDevices = 64;
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kNaState = 0;
+constexpr size_t kNaBad = na_align(sizeof(DevState));
+constexpr size_t kNaArrive = kNaBad + 256;
+constexpr size_t kNaSmid = kNaArrive + na_align(sizeof(int32_t) * kNoAllocMaxCtas);
+constexpr size_t kNaStatus = kNaSmid + na_align(sizeof(int32_t) * kNoAllocMaxCtas);
+constexpr size_t kNaFront = kNaStatus + na_align(sizeof(ChunkStatus) * kNoAllocMaxCtas * kWarpsPerCta);
+constexpr size_t kNaFrontOne = na_align(sizeof(int32_t) * (kNoAllocMaxN + 4));
+constexpr size_t kNaCol = kNaFront + 6 * kNaFrontOne;
+constexpr size_t kNaCand = kNaCol + na_align(sizeof(int32_t) * (kNoAllocMaxNnz + 8));
+constexpr size_t kNoAllocScratchBytes = kNaCand + na_align(sizeof(int2) * (kNoAllocMaxNnz + 32));
+
+// The scratch itself (about 32 MB).  Host code must not use this name as an
+// address: it is a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+  bool ready;
+  unsigned char* scratch;  // device address of g_noalloc_scratch on this device
+  int ctas;
+  int sms;
+};
+static NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Per-device set-up, done by the first call on each device with that device
+// current: look up the scratch address and the persistent grid size.
+static int noalloc_setup(int dev, NoAllocDevice** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr)
+      return fail(BFS_E_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+    int sms = 0, coop = 0, per_sm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return fail(BFS_E_CUDA, "device %d has no cooperative launch", dev);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, 0));
+    if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
+    d.scratch = static_cast<unsigned char*>(ptr);
+    d.sms = sms;
+    d.ctas = std::min(per_sm * sms, kNoAllocMaxCtas);
+    d.ready = true;
+  }
+  *out = &d;
+  return BFS_OK;
+}
+
+extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                                   int32_t src, int32_t* level_out, int32_t* parent_out, void* cuda_stream) {
+  if (n < 1 || n > kNoAllocMaxN)
+    return fail(BFS_E_INVAL, "n = %d: the allocation-free entry point takes 1..%d vertices", n, kNoAllocMaxN);
+  if (nnz < 0 || nnz > kNoAllocMaxNnz)
+    return fail(BFS_E_INVAL, "nnz = %d: the allocation-free entry point takes 0..%d edges", nnz, kNoAllocMaxNnz);
+  if (!row_ptr || (nnz > 0 && !col_idx) || !level_out || !parent_out)
+    return fail(BFS_E_INVAL, "NULL pointer argument");
+  if (src < 0 || src >= n) return fail(BFS_E_INVAL, "src %d out of range [0, %d)", src, n);
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(BFS_E_INVAL, "device %d beyond %d", dev, kNoAllocMaxDevices);
+  NoAllocDevice* d = nullptr;
+  int rc = noalloc_setup(dev, &d);
+  if (rc != BFS_OK) return rc;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  unsigned char* s = d->scratch;
+  int32_t* col = reinterpret_cast<int32_t*>(s + kNaCol);
+  int* bad = reinterpret_cast<int*>(s + kNaBad);
+
+  // copy col_idx into the aligned, padded scratch copy that the 16-byte quad
+  // loads read; then the range checks every later access relies on
+  CUDA_TRY(cudaMemsetAsync(col + (nnz & ~3), 0, sizeof(int32_t) * 8, stream));
+  if (nnz > 0)
+    CUDA_TRY(cudaMemcpyAsync(col, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, stream));
+  CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), stream));
+  const int cgrid = std::max(1, std::min(d->sms * 8, (int)(((long long)std::max(n, nnz) + 255) / 256)));
+  k_check_csr<<<cgrid, 256, 0, stream>>>(n, nnz, row_ptr, col, bad);
+  CUDA_TRY(cudaGetLastError());
+  int h_bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (h_bad == 1) return fail(BFS_E_INVAL, "row_ptr must start at 0, never decrease and end at nnz");
+  if (h_bad == 2) return fail(BFS_E_INVAL, "col_idx entry out of range [0, n)");
+
+  Params p;
+  memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.nnz = nnz;
+  p.row_ptr = row_ptr;
+  p.col_idx = col;
+  p.level = level_out;
+  p.parent = parent_out;
+  for (int b = 0; b < 2; ++b) {
+    p.F[b] = reinterpret_cast<int32_t*>(s + kNaFront + (size_t)(3 * b + 0) * kNaFrontOne);
+    p.RS[b] = reinterpret_cast<int32_t*>(s + kNaFront + (size_t)(3 * b + 1) * kNaFrontOne);
+    p.EX[b] = reinterpret_cast<int32_t*>(s + kNaFront + (size_t)(3 * b + 2) * kNaFrontOne);
+  }
+  p.cand = reinterpret_cast<int2*>(s + kNaCand);
+  p.cand_cnt = nullptr;
+  p.status = reinterpret_cast<ChunkStatus*>(s + kNaStatus);
+  p.bar_arrive = reinterpret_cast<int32_t*>(s + kNaArrive);
+  p.cta_smid = reinterpret_cast<int32_t*>(s + kNaSmid);
+  p.st = reinterpret_cast<DevState*>(s + kNaState);
+  p.lvl = nullptr;
+  p.lvl_cap = 0;
+  p.grain = 256;
+  p.work_insensitive = 0;
+  p.src = src;
+  p.max_chunks = d->ctas * kWarpsPerCta;
+  p.debug_flags = 0;
+  p.spin_ns = 1000000000ll;
+
+  // k_init clears the look-back and barrier state left by the previous call
+  const int igrid = std::max(1, std::min(d->sms * 8, (int)(((long long)n / 4 + 255) / 256)));
+  k_init<<<igrid, kThreads, 0, stream>>>(p, d->ctas);
+  CUDA_TRY(cudaGetLastError());
+  void* args[] = {&p};
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(d->ctas), dim3(kThreads), args, 0, stream));
+  DevState h;
+  CUDA_TRY(cudaMemcpyAsync(&h, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (h.err == BFS_E_TIMEOUT) return fail(BFS_E_TIMEOUT, "device wait %d ran out (src %d)", h.err_where, src);
+  if (h.err == BFS_E_MULTIGRAPH)
+    return fail(BFS_E_MULTIGRAPH, "next frontier larger than n: the graph repeats a neighbour (src %d)", src);
+  if (h.err != 0) return fail(h.err, "device error %d at %d (src %d)", h.err, h.err_where, src);
+  return BFS_OK;
 }
