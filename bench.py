@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--work-insensitive", action="store_true")
     ap.add_argument("--per-phase", action="store_true", help="one launch per phase instead of the persistent loop")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dump", default="", help="write per-traversal records of the timed steps (JSON) here")
+    ap.add_argument("--levels", action="store_true", help="add the per-level statistics of the first source")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.sources:
@@ -261,7 +263,7 @@ def main():
             B.bfs_run(g, int(s), level, parent, st)
             if record is not None:
                 out.append((st.ms_level_step, st.ms_total, st.reached, st.edges_scanned, st.candidates,
-                            st.num_levels))
+                            st.num_levels, int(s)))
         return out
 
     for _ in range(args.warmup):
@@ -324,6 +326,24 @@ def main():
         e2e = {"value": edges_per_step / te / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
                "d2h_bytes_per_step": int(len(srcs) * (8 * n + ctypes.sizeof(ctypes.c_int64) * 8))}
 
+    per_level = None
+    if args.levels:
+        cap = 1 << 16
+        buf = (ctypes.c_int32 * (cap * B.BFS_LEVEL_FIELDS))()
+        st2 = B.bfs_stats()
+        st2.per_level = ctypes.cast(buf, ctypes.POINTER(ctypes.c_int32))
+        st2.per_level_cap = cap
+        B.bfs_run(g, int(srcs[0]), level, parent, st2)
+        L = min(st2.num_levels, cap)
+        rows = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS)
+        per_level = {"src": int(srcs[0]), "fields": ["n_l", "e_l", "c_l", "active_warps", "active_sms", "ns"],
+                     "rows": rows.tolist() if L <= 64 else rows[:64].tolist(), "levels": L,
+                     "ns_total": int(rows[:, 5].sum())}
+    if args.dump and rank == 0:
+        with open(args.dump, "w") as f:
+            json.dump([{"src": int(r[6]), "ms_level_step": r[0], "ms_total": r[1], "reached": int(r[2]),
+                        "edges_scanned": int(r[3]), "candidates": int(r[4]), "levels": int(r[5]),
+                        "algorithmic_bytes": float(8 * r[3] + 32 * r[2] + 28 * r[4])} for r in recs.tolist()], f)
     if rank == 0:
         line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -336,6 +356,8 @@ def main():
                 "ctas": info["ctas"], "warps": info["warps"]}
         if e2e:
             line["e2e"] = e2e
+        if per_level:
+            line["per_level"] = per_level
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, rp, ci, srcs, args.cpu_budget)
         print(json.dumps(line), flush=True)

@@ -47,7 +47,7 @@ typedef struct bfs_opts {
   int32_t chunk_edges;      /* grain: minimum edges per warp chunk.  Level l runs
                                P_l = min(P, ceil(e_l / chunk_edges)) warps, the
                                work-sensitive count of Fig. 1 lines 11/16 (the
-                               paper's own formula is chunk_edges = 1).  Default 256 */
+                               paper's own formula is chunk_edges = 1).  Default 64 */
   int32_t ctas;             /* persistent grid size G (CTAs of 256 threads); 0 = every
                                CTA that can be co-resident on the device */
   int32_t persistent;       /* 1 (default): one cooperative launch runs all levels,
@@ -61,12 +61,14 @@ typedef struct bfs_opts {
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */
-#define BFS_LEVEL_FIELDS 5
+#define BFS_LEVEL_FIELDS 6
 /* [0] n_l          frontier size (vertices at distance l)
  * [1] e_l          edges the level scans (sum of frontier out-degrees)
  * [2] c_l          candidates emitted by the explore step (n_{l+1} <= c_l <= e_l)
  * [3] active_warps P_l, warps that explored this level
- * [4] active_sms   distinct SMs hosting those warps */
+ * [4] active_sms   distinct SMs hosting those warps (-1 with one launch per phase)
+ * [5] ns           device time of the level, explore to the end of the compact
+ *                  barrier, from the global timer (-1 with one launch per phase) */
 
 /* Statistics of one traversal (all optional). */
 typedef struct bfs_stats {
@@ -174,7 +176,7 @@ int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, 
  * with the meaning of bfs_run.  cuda_stream as for bfs_create_csr.  Blocks until
  * the traversal is complete.
  *
- * Working memory: one static device array of about 32 MB that every GPU
+ * Working memory: one static device array of about 40 MB that every GPU
  * loading this library's device code reserves until the process exits.  It
  * bounds the sizes: 1 <= n <= 262,144 and 0 <= nnz <= 2,097,152; larger graphs
  * are rejected with BFS_E_INVAL and a message in bfs_last_error().  The CSR is

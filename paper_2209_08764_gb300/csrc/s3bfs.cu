@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
     }
   }
   for (long long i = tid; i < p.max_chunks; i += stride) p.status[i].word = 0ull;
-  for (long long i = tid; i < ctas; i += stride) p.bar_arrive[i] = 0;
+  for (long long i = tid; i < ((ctas + 3) & ~3); i += stride) p.bar_arrive[i] = 0;
   if (tid == 0) {
     const int rs = p.row_ptr[s], deg = p.row_ptr[s + 1] - rs;
     p.F[0][0] = s;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
 // The whole level loop in one cooperative launch: explore, grid barrier,
 // compact, grid barrier, per level.  Warps beyond P_l skip the level's work
 // and wait at the barrier (parked), so a small level occupies few SMs.
-__global__ void __launch_bounds__(kThreads) k_level_loop(Params p) {
+__global__ void __launch_bounds__(kThreads, S3BFS_MIN_CTAS) k_level_loop(Params p) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int P = gridDim.x * kWarpsPerCta;
@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(kThreads) k_level_loop(Params p) {
     }
     int P_l, C_l;
     level_sizing(e_l, P, p.grain, p.work_insensitive, &P_l, &C_l);
+    long long t_level = 0;
     if (leader) {
+      t_level = global_ns();
       reached += n_l;
       edges += e_l;
       record_level(p, l, n_l, e_l, P_l);
@@ -120,11 +122,14 @@ __global__ void __launch_bounds__(kThreads) k_level_loop(Params p) {
     if (!grid_sync(p, ++bar)) break;
     if (P_l == 0) {
       if (gw == 0 && lane == 0) publish_empty_next(p, par);
-    } else if (gw < P_l) {
-      compact_chunk(p, l, par, gw, P_l, p.cand + e_begin, cnt);
+    } else if ((int)blockIdx.x * kWarpsPerCta < P_l) {
+      compact_cta(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
     }
     if (!grid_sync(p, ++bar)) break;
-    if (leader) cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+    if (leader) {
+      cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+      if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
+    }
     ++l;
   }
   if (leader) {
@@ -156,10 +161,10 @@ __global__ void __launch_bounds__(kThreads) k_compact(Params p, int l, int e_l, 
     if (gw == 0 && (threadIdx.x & (kWarp - 1)) == 0) publish_empty_next(p, par);
     return;
   }
-  if (gw >= P_l) return;
-  const int e_begin = (int)min((long long)gw * C_l, (long long)e_l);
-  const int cnt = ld_relaxed(&p.cand_cnt[gw]);
-  compact_chunk(p, l, par, gw, P_l, p.cand + e_begin, cnt);
+  // every thread of the CTA takes part; warps without a chunk bring 0
+  const int e_begin = gw < P_l ? (int)min((long long)gw * C_l, (long long)e_l) : 0;
+  const int cnt = gw < P_l ? ld_relaxed(&p.cand_cnt[gw]) : 0;
+  compact_cta(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
 }
 
 // CSR sanity checks that every traversal relies on (no out-of-range access):
@@ -185,7 +190,7 @@ struct bfs_graph {
   int sms = 0;
   int ctas = 0;   // G
   int warps = 0;  // P
-  int grain = 256;
+  int grain = 64;
   int persistent = 1;
   int work_insensitive = 0;
   int debug_flags = 0;
@@ -195,6 +200,7 @@ struct bfs_graph {
   int32_t *d_level = nullptr, *d_parent = nullptr;
   int32_t *d_F[2] = {nullptr, nullptr}, *d_RS[2] = {nullptr, nullptr}, *d_EX[2] = {nullptr, nullptr};
   int2* d_cand = nullptr;
+  int32_t* d_cand_aux = nullptr;
   int32_t* d_cand_cnt = nullptr;
   ChunkStatus* d_status = nullptr;
   int32_t *d_arrive = nullptr, *d_smid = nullptr;
@@ -363,9 +369,10 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     if ((rc = dalloc(g, &g->d_EX[b], (size_t)n + 4)) != BFS_OK) return rc;
   }
   if ((rc = dalloc(g, &g->d_cand, (size_t)nnz + 32)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_cand_aux, (size_t)nnz + 32)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_cand_cnt, (size_t)max_chunks)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_status, (size_t)max_chunks)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_arrive, (size_t)g->ctas)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_arrive, (size_t)(g->ctas + 3) / 4 * 4)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_smid, (size_t)g->ctas)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_st, 1)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_lvl, (size_t)g->lvl_cap * kLevelFields)) != BFS_OK) return rc;
@@ -432,6 +439,7 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
     p.EX[b] = g->d_EX[b];
   }
   p.cand = g->d_cand;
+  p.cand_aux = g->d_cand_aux;
   p.cand_cnt = g->d_cand_cnt;
   p.status = g->d_status;
   p.bar_arrive = g->d_arrive;
@@ -552,6 +560,7 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
       int32_t* r = stats->per_level + (size_t)l * kLevelFields;
       const int ctas = std::min(g->ctas, (r[3] + kWarpsPerCta - 1) / kWarpsPerCta);
       r[4] = g->persistent ? distinct[ctas] : -1;
+      if (!g->persistent) r[5] = -1;
     }
   }
   return BFS_OK;
@@ -637,9 +646,10 @@ constexpr size_t kNaFront = kNaStatus + na_align(sizeof(ChunkStatus) * kNoAllocM
 constexpr size_t kNaFrontOne = na_align(sizeof(int32_t) * (kNoAllocMaxN + 4));
 constexpr size_t kNaCol = kNaFront + 6 * kNaFrontOne;
 constexpr size_t kNaCand = kNaCol + na_align(sizeof(int32_t) * (kNoAllocMaxNnz + 8));
-constexpr size_t kNoAllocScratchBytes = kNaCand + na_align(sizeof(int2) * (kNoAllocMaxNnz + 32));
+constexpr size_t kNaAux = kNaCand + na_align(sizeof(int2) * (kNoAllocMaxNnz + 32));
+constexpr size_t kNoAllocScratchBytes = kNaAux + na_align(sizeof(int32_t) * (kNoAllocMaxNnz + 32));
 
-// The scratch itself (about 32 MB).  Host code must not use this name as an
+// The scratch itself (about 40 MB).  Host code must not use this name as an
 // address: it is a host-side stand-in; the device address comes from
 // cudaGetSymbolAddress, once per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -727,6 +737,7 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
     p.EX[b] = reinterpret_cast<int32_t*>(s + kNaFront + (size_t)(3 * b + 2) * kNaFrontOne);
   }
   p.cand = reinterpret_cast<int2*>(s + kNaCand);
+  p.cand_aux = reinterpret_cast<int32_t*>(s + kNaAux);
   p.cand_cnt = nullptr;
   p.status = reinterpret_cast<ChunkStatus*>(s + kNaStatus);
   p.bar_arrive = reinterpret_cast<int32_t*>(s + kNaArrive);
@@ -734,7 +745,7 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   p.st = reinterpret_cast<DevState*>(s + kNaState);
   p.lvl = nullptr;
   p.lvl_cap = 0;
-  p.grain = 256;
+  p.grain = 64;
   p.work_insensitive = 0;
   p.src = src;
   p.max_chunks = d->ctas * kWarpsPerCta;

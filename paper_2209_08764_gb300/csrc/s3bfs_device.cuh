@@ -33,6 +33,23 @@
 
 #include "s3bfs.h"
 
+// Build-time knobs (tuning experiments).
+#ifndef S3BFS_LEVEL_CACHED
+#define S3BFS_LEVEL_CACHED 1  // 1: level[v] tests through L1 (weak loads), 0: relaxed loads at L2
+#endif
+#ifndef S3BFS_COL_EVICT_FIRST
+#define S3BFS_COL_EVICT_FIRST 1  // 1: col_idx streamed with an L2 evict-first policy, no L1 allocation
+#endif
+#ifndef S3BFS_QPL
+#define S3BFS_QPL 2  // col_idx quads per lane per round of the explore walk
+#endif
+#ifndef S3BFS_CR
+#define S3BFS_CR 2  // candidates per lane per batch of the compaction
+#endif
+#ifndef S3BFS_MIN_CTAS
+#define S3BFS_MIN_CTAS 4  // __launch_bounds__ minimum CTAs per SM of the level loop (64 registers)
+#endif
+
 namespace s3bfs {
 
 constexpr int kWarp = 32;
@@ -47,9 +64,9 @@ constexpr unsigned long long kFlagAgg = 1ull;
 constexpr unsigned long long kFlagIncl = 2ull;
 constexpr unsigned kEpochMask = 0x3FFFFFFFu;
 
-// Look-back state of one chunk: word = [63:62] flag, [61:32] epoch (level+1),
-// [31:0] kept count.  The degree and candidate sums sit in separate slots for
-// the aggregate and the inclusive prefix, written before the word is released.
+// Scan state of one CTA of a level: word = [63:62] flag, [61:32] epoch
+// (level+1), [31:0] kept count; the degree and candidate sums sit in slots
+// written before the word is released.
 struct alignas(32) ChunkStatus {
   unsigned long long word;
   int32_t agg_deg, agg_cand, incl_deg, incl_cand;
@@ -80,8 +97,9 @@ struct Params {
   int32_t* RS[2];
   int32_t* EX[2];
   int2* cand;           // candidate pairs (v, u); chunk k owns [k*C_l, (k+1)*C_l)
+  int32_t* cand_aux;    // per candidate slot: degree prefix of a stashed survivor
   int32_t* cand_cnt;    // per chunk, for the launch-per-phase mode
-  ChunkStatus* status;  // per chunk
+  ChunkStatus* status;  // per CTA
   int32_t* bar_arrive;  // per CTA
   int32_t* cta_smid;    // per CTA
   DevState* st;
@@ -141,6 +159,50 @@ __device__ __forceinline__ int4 ld_nc4(const int4* p) {
                : "l"(p));
   return v;
 }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int4 ld_relaxed4(const int4* p) {
+  int4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+// level[v] test of the explore walk.  Within a level a stale -1 only adds a
+// duplicate candidate (removed by the dedup); across levels the acquire at
+// the grid barrier makes every earlier write visible.
+__device__ __forceinline__ int ld_level(const int* p) {
+#if S3BFS_LEVEL_CACHED
+  int v;
+  asm volatile("ld.global.ca.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+#else
+  return ld_relaxed_nb(p);
+#endif
+}
+__device__ __forceinline__ unsigned long long col_policy() {
+  unsigned long long pol = 0;
+#if S3BFS_COL_EVICT_FIRST
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+#endif
+  return pol;
+}
+__device__ __forceinline__ int4 ld_col4(const int4* p, unsigned long long pol) {
+#if S3BFS_COL_EVICT_FIRST
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return ld_nc4(p);
+#endif
+}
 __device__ __forceinline__ long long global_ns() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -199,11 +261,20 @@ __device__ bool grid_sync(const Params& p, int epoch) {
     if (!stall) st_relaxed(&p.bar_arrive[blockIdx.x], epoch);
   }
   if (blockIdx.x == 0) {
+    // CTA 0 gathers the arrivals, four words per 16-byte load (the arrival
+    // array is padded to a multiple of four entries)
     bool ok = true;
     const long long t0 = global_ns();
-    for (int j = threadIdx.x; j < (int)gridDim.x && ok; j += blockDim.x) {
+    const int groups = ((int)gridDim.x + 3) >> 2;
+    const int4* arr4 = reinterpret_cast<const int4*>(p.bar_arrive);
+    for (int q = threadIdx.x; q < groups && ok; q += blockDim.x) {
+      const int base = q << 2;
       int it = 0;
-      while (ld_relaxed(&p.bar_arrive[j]) < epoch) {
+      while (true) {
+        const int4 a = ld_relaxed4(arr4 + q);
+        const bool done = (a.x >= epoch || base + 0 >= (int)gridDim.x) && (a.y >= epoch || base + 1 >= (int)gridDim.x) &&
+                          (a.z >= epoch || base + 2 >= (int)gridDim.x) && (a.w >= epoch || base + 3 >= (int)gridDim.x);
+        if (done) break;
         if (ld_relaxed(&p.st->err) != 0) {
           ok = false;
           break;
@@ -225,7 +296,7 @@ __device__ bool grid_sync(const Params& p, int epoch) {
   if (threadIdx.x == 0) {
     int ok = 1, it = 0;
     const long long t0 = global_ns();
-    while (ld_relaxed(&p.st->bar_release) < epoch) {
+    while (ld_acquire(&p.st->bar_release) < epoch) {
       if (ld_relaxed(&p.st->err) != 0) {
         ok = 0;
         break;
@@ -270,6 +341,7 @@ __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, 
   int* level = p.level;
   int* parent = p.parent;
   const int lnext = l + 1;
+  const unsigned long long pol = col_policy();
 
   // Find-StartExpPoint (line 17): the last frontier entry i with EX[i] <=
   // e_begin (upper bound minus one), by a 32-ary search -- every round the
@@ -315,45 +387,53 @@ __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, 
     const int qoff = qend - nq;
     // Load-balanced walk: round r hands quad r*32+lane to this lane; its owner
     // entry w is the first lane whose quad range ends after it.
-    for (int base = 0; base < Q; base += kWarp) {
-      const int q = base + lane;
-      int w = 0;
+    for (int base = 0; base < Q; base += kWarp * S3BFS_QPL) {
+      int4 c[S3BFS_QPL];
+      int wp0[S3BFS_QPL], wp1[S3BFS_QPL], wu[S3BFS_QPL], pos[S3BFS_QPL];
 #pragma unroll
-      for (int s = 16; s >= 1; s >>= 1) {
-        const int t = __shfl_sync(kFull, qend, w + s - 1);
-        if (t <= q) w += s;
+      for (int r = 0; r < S3BFS_QPL; ++r) {
+        const int q = base + r * kWarp + lane;
+        int w = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+          const int t = __shfl_sync(kFull, qend, w + s - 1);
+          if (t <= q) w += s;
+        }
+        const bool act = q < Q;
+        const int wq0 = __shfl_sync(kFull, q0, w);
+        const int wqoff = __shfl_sync(kFull, qoff, w);
+        wp0[r] = __shfl_sync(kFull, p0, w);
+        wp1[r] = __shfl_sync(kFull, p1, w);
+        wu[r] = __shfl_sync(kFull, u, w);
+        const int qa = wq0 + (q - wqoff);
+        c[r] = make_int4(0, 0, 0, 0);
+        if (act) c[r] = ld_col4(col4 + qa, pol);
+        pos[r] = act ? (qa << 2) : 0x7FFFFFF0;   // inactive: no position is valid
       }
-      const bool act = q < Q;
-      const int wq0 = __shfl_sync(kFull, q0, w);
-      const int wqoff = __shfl_sync(kFull, qoff, w);
-      const int wp0 = __shfl_sync(kFull, p0, w);
-      const int wp1 = __shfl_sync(kFull, p1, w);
-      const int wu = __shfl_sync(kFull, u, w);
-      const int qa = wq0 + (q - wqoff);
-      int4 c = make_int4(0, 0, 0, 0);
-      if (act) c = ld_nc4(col4 + qa);
-      const int pos = qa << 2;
-      const bool v0 = act && pos >= wp0 && pos < wp1;
-      const bool v1 = act && pos + 1 >= wp0 && pos + 1 < wp1;
-      const bool v2 = act && pos + 2 >= wp0 && pos + 2 < wp1;
-      const bool v3 = act && pos + 3 >= wp0 && pos + 3 < wp1;
-      int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
-      if (v0) l0 = ld_relaxed_nb(level + c.x);
-      if (v1) l1 = ld_relaxed_nb(level + c.y);
-      if (v2) l2 = ld_relaxed_nb(level + c.z);
-      if (v3) l3 = ld_relaxed_nb(level + c.w);
-      const bool k0 = v0 && l0 < 0;
-      const bool k1 = v1 && l1 < 0;
-      const bool k2 = v2 && l2 < 0;
-      const bool k3 = v3 && l3 < 0;
-      if (k0) { st_relaxed(level + c.x, lnext); st_relaxed(parent + c.x, wu); }
-      if (k1) { st_relaxed(level + c.y, lnext); st_relaxed(parent + c.y, wu); }
-      if (k2) { st_relaxed(level + c.z, lnext); st_relaxed(parent + c.z, wu); }
-      if (k3) { st_relaxed(level + c.w, lnext); st_relaxed(parent + c.w, wu); }
-      cnt = emit(out, cnt, k0, c.x, wu, lane);
-      cnt = emit(out, cnt, k1, c.y, wu, lane);
-      cnt = emit(out, cnt, k2, c.z, wu, lane);
-      cnt = emit(out, cnt, k3, c.w, wu, lane);
+      int lv[S3BFS_QPL][4];
+      bool vv[S3BFS_QPL][4];
+#pragma unroll
+      for (int r = 0; r < S3BFS_QPL; ++r) {
+        const int cc[4] = {c[r].x, c[r].y, c[r].z, c[r].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          vv[r][j] = pos[r] + j >= wp0[r] && pos[r] + j < wp1[r];
+          lv[r][j] = vv[r][j] ? ld_level(level + cc[j]) : 0;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < S3BFS_QPL; ++r) {
+        const int cc[4] = {c[r].x, c[r].y, c[r].z, c[r].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool k = vv[r][j] && lv[r][j] < 0;
+          if (k) {
+            st_relaxed(level + cc[j], lnext);
+            st_relaxed(parent + cc[j], wu[r]);
+          }
+          cnt = emit(out, cnt, k, cc[j], wu[r], lane);
+        }
+      }
     }
     // advance past the entries whose edges are all done
     i += __popc(__ballot_sync(kFull, in && ex_hi <= tile_end));
@@ -363,152 +443,208 @@ __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, 
 }
 
 // ---------------------------------------------------------------------------
-// COMPACT: decoupled look-back over the chunks of one level
+// COMPACT: dedup, then a single-pass look-back scan over the CTAs of a level
 // ---------------------------------------------------------------------------
 
-// Publishes chunk k's aggregate (kept count K, kept degree sum D, candidates
-// C), accumulates the predecessors' values (32 at a time, stopping at the
-// nearest inclusive prefix) and publishes k's inclusive prefix.
-__device__ bool lookback(const Params& p, int k, int epoch, int K, int D, int C, int* Kx, int* Dx,
-                         int* Cx) {
-  const int lane = threadIdx.x & (kWarp - 1);
-  ChunkStatus* S = p.status;
-  const unsigned long long ep = (unsigned long long)((unsigned)epoch & kEpochMask) << 32;
-  if (lane == 0) {
-    if (k == 0) {
-      S[0].incl_deg = D;
-      S[0].incl_cand = C;
-      st_release64(&S[0].word, (kFlagIncl << 62) | ep | (unsigned)K);
-    } else {
-      S[k].agg_deg = D;
-      S[k].agg_cand = C;
-      st_release64(&S[k].word, (kFlagAgg << 62) | ep | (unsigned)K);
-    }
-  }
-  int kx = 0, dx = 0, cx = 0;
-  if (k > 0) {
-    int j = k - 1;
-    const long long t0 = global_ns();
-    while (true) {
-      const int idx = j - lane;
-      unsigned long long w = 0;
-      bool ok = true;
-      if (idx >= 0) {
-        int it = 0;
-        while (true) {
-          w = ld_acquire64(&S[idx].word);
-          if ((unsigned)((w >> 32) & kEpochMask) == ((unsigned)epoch & kEpochMask) && (w >> 62) != 0) break;
-          if (ld_relaxed(&p.st->err) != 0) {
-            ok = false;
-            break;
-          }
-          if (++it > kSpinIters || global_ns() - t0 > p.spin_ns) {
-            set_err(p, BFS_E_TIMEOUT, 3);
-            ok = false;
-            break;
-          }
-          if (it > 32) __nanosleep(32);
-        }
-      }
-      if (__any_sync(kFull, !ok)) return false;
-      const unsigned long long flag = idx >= 0 ? (w >> 62) : 0ull;
-      const unsigned incl = __ballot_sync(kFull, flag == kFlagIncl);
-      const int stop = incl ? __ffs(incl) - 1 : kWarp - 1;
-      int kk = 0, dd = 0, cc = 0;
-      if (idx >= 0 && lane <= stop) {
-        kk = (int)(unsigned)(w & 0xffffffffull);
-        if (flag == kFlagIncl) {
-          dd = ld_relaxed(&S[idx].incl_deg);
-          cc = ld_relaxed(&S[idx].incl_cand);
-        } else {
-          dd = ld_relaxed(&S[idx].agg_deg);
-          cc = ld_relaxed(&S[idx].agg_cand);
-        }
-      }
-      kx += __reduce_add_sync(kFull, kk);
-      dx += __reduce_add_sync(kFull, dd);
-      cx += __reduce_add_sync(kFull, cc);
-      if (incl) break;
-      j -= kWarp;
-    }
-    if (lane == 0) {
-      S[k].incl_deg = dx + D;
-      S[k].incl_cand = cx + C;
-      st_release64(&S[k].word, (kFlagIncl << 62) | ep | (unsigned)(kx + K));
-    }
-  }
-  *Kx = kx;
-  *Dx = dx;
-  *Cx = cx;
-  return true;
-}
+// Dedup (lines 19-23) and linearisation (lines 24-29) of the candidates of one
+// CTA's chunks, plus the degree gather and exclusive scan of the next frontier
+// (lines 12-15 of the next level).  Called by every thread of a CTA that holds
+// at least one of the level's P_l chunks; warps without a chunk pass cnt = 0.
+//
+// Pass 1 (per warp): candidates 128 at a time (S3BFS_CR per lane), all loads
+// in flight together; keep (v, u) iff parent[v] == u.  Survivors of the last
+// batch stay in registers, earlier batches are stashed in place (kept index <=
+// candidate index) as (v, row start) in cand with their degree prefix in aux.
+// Scan: the CTA's aggregate (kept count, kept degree sum, candidates) is
+// published with a release store; every CTA then sums the aggregates of all
+// CTAs before it (256 at a time, no chain of inclusive prefixes to wait for)
+// and adds its warps' offsets.  Pass 2 writes the survivors at their slots of
+// the next frontier F / RS / EX.  The CTA holding chunk P_l - 1 publishes the
+// next level's n and e.  Returns false (in every thread) if a wait ran out.
+constexpr int kCompactR = S3BFS_CR;
 
-// Dedup (lines 19-23) and linearisation (lines 24-29) of chunk k's candidate
-// pairs cand[0, cnt), plus the degree gather and exclusive scan of the next
-// frontier (lines 12-15 of the next level).  The last chunk publishes the
-// next level's n and e.  Returns false if a wait ran out.
-__device__ bool compact_chunk(const Params& p, int l, int par, int k, int P_l, const int2* cand, int cnt) {
+__device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt) {
+  __shared__ int sK[kWarpsPerCta], sD[kWarpsPerCta], sC[kWarpsPerCta];
+  __shared__ int sRed[3][kWarpsPerCta];
+  __shared__ int sPre[3];
   const int lane = threadIdx.x & (kWarp - 1);
+  const int wib = threadIdx.x >> 5;
+  const int b = blockIdx.x;
   const int np = par ^ 1;
   int* Fn = np ? p.F[1] : p.F[0];
   int* RSn = np ? p.RS[1] : p.RS[0];
   int* EXn = np ? p.EX[1] : p.EX[0];
   const unsigned lt = (1u << lane) - 1u;
-  // pass 1: this chunk's survivors and their degree sum
-  int K = 0, D = 0;
-  for (int base = 0; base < cnt; base += kWarp) {
-    const int j = base + lane;
-    bool keep = false;
-    int deg = 0;
-    if (j < cnt) {
-      const int2 pr = ld_cg2(cand + j);
-      keep = ld_relaxed_nb(p.parent + pr.x) == pr.y;
-      if (keep) deg = __ldg(p.row_ptr + pr.x + 1) - __ldg(p.row_ptr + pr.x);
+
+  // ---- pass 1
+  int K = 0, D = 0, K_stash = 0;
+  int v[kCompactR], rs[kCompactR], idx[kCompactR], dpre[kCompactR];
+  bool keep[kCompactR];
+#pragma unroll
+  for (int r = 0; r < kCompactR; ++r) keep[r] = false;
+  for (int base = 0; base < cnt; base += kWarp * kCompactR) {
+    int2 pr[kCompactR];
+    int pv[kCompactR], re[kCompactR];
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r) {
+      const int j = base + r * kWarp + lane;
+      pr[r] = j < cnt ? ld_cg2(cand + j) : make_int2(0, -2);
     }
-    K += __popc(__ballot_sync(kFull, keep));
-    D += __reduce_add_sync(kFull, deg);
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r)
+      pv[r] = pr[r].y != -2 ? ld_relaxed_nb(p.parent + pr[r].x) : -3;
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r) {
+      keep[r] = pv[r] == pr[r].y;
+      v[r] = pr[r].x;
+      rs[r] = keep[r] ? __ldg(p.row_ptr + v[r]) : 0;
+      re[r] = keep[r] ? __ldg(p.row_ptr + v[r] + 1) : 0;
+    }
+    K_stash = K;
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r) {
+      const int deg = re[r] - rs[r];
+      const unsigned m = __ballot_sync(kFull, keep[r]);
+      const int incl = warp_incl_scan(deg, lane);
+      idx[r] = K + __popc(m & lt);
+      dpre[r] = D + incl - deg;
+      K += __popc(m);
+      D += __shfl_sync(kFull, incl, kWarp - 1);
+    }
+    if (base + kWarp * kCompactR < cnt) {
+#pragma unroll
+      for (int r = 0; r < kCompactR; ++r)
+        if (keep[r]) {
+          cand[idx[r]] = make_int2(v[r], rs[r]);
+          aux[idx[r]] = dpre[r];
+        }
+    }
   }
-  int Kx, Dx, Cx;
-  if (!lookback(p, k, l + 1, K, D, cnt, &Kx, &Dx, &Cx)) return false;
-  // pass 2: write the survivors at their global slots
-  int kb = Kx, db = Dx;
-  for (int base = 0; base < cnt; base += kWarp) {
-    const int j = base + lane;
-    bool keep = false;
-    int deg = 0, rs = 0, v = 0;
-    if (j < cnt) {
-      const int2 pr = ld_cg2(cand + j);
-      v = pr.x;
-      keep = ld_relaxed_nb(p.parent + v) == pr.y;
-      if (keep) {
-        rs = __ldg(p.row_ptr + v);
-        deg = __ldg(p.row_ptr + v + 1) - rs;
+  if (lane == 0) {
+    sK[wib] = K;
+    sD[wib] = D;
+    sC[wib] = cnt;
+  }
+  __syncthreads();
+
+  // ---- scan over the CTAs of this level
+  ChunkStatus* S = p.status;
+  const unsigned long long ep = (unsigned long long)((unsigned)(l + 1) & kEpochMask) << 32;
+  if (threadIdx.x == 0) {
+    int Kc = 0, Dc = 0, Cc = 0;
+#pragma unroll
+    for (int w = 0; w < kWarpsPerCta; ++w) {
+      Kc += sK[w];
+      Dc += sD[w];
+      Cc += sC[w];
+    }
+    S[b].agg_deg = Dc;
+    S[b].agg_cand = Cc;
+    st_release64(&S[b].word, (kFlagAgg << 62) | ep | (unsigned)Kc);
+  }
+  int kk = 0, dd = 0, cc = 0;
+  bool ok = true;
+  const long long t0 = global_ns();
+  for (int j = threadIdx.x; j < b && ok; j += blockDim.x) {
+    int it = 0;
+    unsigned long long w;
+    while (true) {
+      w = ld_acquire64(&S[j].word);
+      if ((unsigned)((w >> 32) & kEpochMask) == ((unsigned)(l + 1) & kEpochMask) && (w >> 62) != 0) break;
+      if (ld_relaxed(&p.st->err) != 0) {
+        ok = false;
+        break;
+      }
+      if (++it > kSpinIters || global_ns() - t0 > p.spin_ns) {
+        set_err(p, BFS_E_TIMEOUT, 3);
+        ok = false;
+        break;
+      }
+      if (it > 32) __nanosleep(32);
+    }
+    if (ok) {
+      kk += (int)(unsigned)(w & 0xffffffffull);
+      dd += ld_relaxed(&S[j].agg_deg);
+      cc += ld_relaxed(&S[j].agg_cand);
+    }
+  }
+  kk = __reduce_add_sync(kFull, kk);
+  dd = __reduce_add_sync(kFull, dd);
+  cc = __reduce_add_sync(kFull, cc);
+  if (lane == 0) {
+    sRed[0][wib] = kk;
+    sRed[1][wib] = dd;
+    sRed[2][wib] = cc;
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok) return false;
+  if (threadIdx.x == 0) {
+    int a = 0, d = 0, c = 0;
+#pragma unroll
+    for (int w = 0; w < kWarpsPerCta; ++w) {
+      a += sRed[0][w];
+      d += sRed[1][w];
+      c += sRed[2][w];
+    }
+    sPre[0] = a;
+    sPre[1] = d;
+    sPre[2] = c;
+  }
+  __syncthreads();
+  int Kx = sPre[0], Dx = sPre[1];
+  for (int w = 0; w < wib; ++w) {
+    Kx += sK[w];
+    Dx += sD[w];
+  }
+
+  // ---- pass 2: stashed batches (a copy with offsets), then the register batch
+  for (int base = 0; base < K_stash; base += kWarp * kCompactR) {
+    int2 sv[kCompactR];
+    int sd[kCompactR];
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r) {
+      const int i = base + r * kWarp + lane;
+      if (i < K_stash) {
+        sv[r] = ld_cg2(cand + i);
+        sd[r] = ld_cg(aux + i);
       }
     }
-    const unsigned m = __ballot_sync(kFull, keep);
-    const int dincl = warp_incl_scan(deg, lane);
-    if (keep) {
-      const int pos = kb + __popc(m & lt);
-      if (pos < p.n) {
-        Fn[pos] = v;
-        RSn[pos] = rs;
-        EXn[pos] = db + dincl - deg;
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r) {
+      const int i = base + r * kWarp + lane;
+      const int pos = Kx + i;
+      if (i < K_stash && pos < p.n) {
+        Fn[pos] = sv[r].x;
+        RSn[pos] = sv[r].y;
+        EXn[pos] = Dx + sd[r];
       }
     }
-    kb += __popc(m);
-    db += __shfl_sync(kFull, dincl, kWarp - 1);
   }
-  if (k == P_l - 1 && lane == 0) {
-    const long long n_next = (long long)Kx + K;
-    const long long e_next = (long long)Dx + D;
-    if (n_next > p.n || e_next > p.nnz) {
+#pragma unroll
+  for (int r = 0; r < kCompactR; ++r) {
+    const int pos = Kx + idx[r];
+    if (keep[r] && pos < p.n) {
+      Fn[pos] = v[r];
+      RSn[pos] = rs[r];
+      EXn[pos] = Dx + dpre[r];
+    }
+  }
+  if (b == (P_l - 1) / kWarpsPerCta && threadIdx.x == 0) {
+    long long n_next = sPre[0], e_next = sPre[1], c_l = sPre[2];
+#pragma unroll
+    for (int w = 0; w < kWarpsPerCta; ++w) {
+      n_next += sK[w];
+      e_next += sD[w];
+      c_l += sC[w];
+    }
+    if (n_next > p.n || e_next > p.nnz || e_next < 0) {
       set_err(p, BFS_E_MULTIGRAPH, 4);
     } else {
       EXn[n_next] = (int)e_next;
       st_relaxed(&p.st->ctrl[np].n, (int)n_next);
       st_relaxed(&p.st->ctrl[np].e, (int)e_next);
-      st_relaxed(&p.st->ctrl[np].c, Cx + cnt);
-      if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 2] = Cx + cnt;
+      st_relaxed(&p.st->ctrl[np].c, (int)c_l);
+      if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 2] = (int)c_l;
     }
   }
   return true;
@@ -529,6 +665,7 @@ __device__ __forceinline__ void record_level(const Params& p, int l, int n_l, in
     r[2] = 0;
     r[3] = P_l;
     r[4] = 0;
+    r[5] = 0;
   }
 }
 

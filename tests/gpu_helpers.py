@@ -50,7 +50,7 @@ class Dev:
         self.g = None
 
 
-def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=256):
+def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=64):
     """Levels bit-exact, parents a valid BFS tree, per-level statistics
     consistent with the oracle's level profile."""
     orc = orc or oracle.Oracle(dev.rp, dev.ci)

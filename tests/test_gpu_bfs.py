@@ -110,7 +110,7 @@ def test_rmat16_launch_configurations(rmat16, opts):
     orc = oracle.Oracle(rp, ci)
     try:
         for s in srcs[:6]:
-            check_against_oracle(d, int(s), orc=orc, keys=keys, grain=opts.get("chunk_edges", 256))
+            check_against_oracle(d, int(s), orc=orc, keys=keys, grain=opts.get("chunk_edges", 64))
     finally:
         d.close()
 
