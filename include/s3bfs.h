@@ -58,6 +58,12 @@ typedef struct bfs_opts {
                                Experimental Results */
   int32_t spin_limit_ms;    /* limit of every device-side wait; default 1000 ms */
   int32_t debug_flags;      /* BFS_DEBUG_* (tests only); default 0 */
+  int32_t relabel;          /* visited bits in shared memory: 0 (default) = for every
+                               vertex when n <= 2^18, else for the 2^18 highest-degree
+                               vertices after a degree-descending renumbering, when
+                               they hold >= half of the edge endpoints; 1 = always
+                               renumber; -1 = neither.  Renumbering is internal:
+                               inputs and outputs keep the caller's vertex ids */
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */

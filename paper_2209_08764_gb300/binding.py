@@ -41,6 +41,7 @@ class bfs_opts(ctypes.Structure):
         ("work_insensitive", ctypes.c_int32),
         ("spin_limit_ms", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
+        ("relabel", ctypes.c_int32),
     ]
 
 

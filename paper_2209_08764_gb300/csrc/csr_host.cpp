@@ -60,3 +60,55 @@ int s3bfs_host_dedup(int32_t n, const int32_t* rp, const int32_t* ci, std::vecto
   }
   return 0;
 }
+
+// Share of all edge endpoints (sum of degrees) held by the `top` vertices of
+// highest degree.
+double s3bfs_host_top_degree_share(int32_t n, const int32_t* rp, int32_t top) {
+  if (n <= 0 || rp[n] <= 0) return 0.0;
+  if (top >= n) return 1.0;
+  int32_t maxd = 0;
+  for (int32_t v = 0; v < n; ++v) maxd = std::max(maxd, rp[v + 1] - rp[v]);
+  std::vector<int64_t> cnt((size_t)maxd + 1, 0);
+  for (int32_t v = 0; v < n; ++v) cnt[(size_t)(rp[v + 1] - rp[v])]++;
+  int64_t left = top, sum = 0;
+  for (int32_t d = maxd; d >= 0 && left > 0; --d) {
+    const int64_t take = std::min<int64_t>(left, cnt[(size_t)d]);
+    sum += take * d;
+    left -= take;
+  }
+  return (double)sum / (double)rp[n];
+}
+
+// Degree-descending renumbering (ties by id): perm[i] is the caller's id of
+// internal vertex i, inv[v] the internal id of v.  The renumbered CSR lists
+// internal rows in order, with every neighbour translated through inv.
+// Returns 0, or -1 if host memory ran out.
+int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* perm,
+                       std::vector<int32_t>* inv, std::vector<int32_t>* rp_out, std::vector<int32_t>* ci_out) {
+  try {
+    int32_t maxd = 0;
+    for (int32_t v = 0; v < n; ++v) maxd = std::max(maxd, rp[v + 1] - rp[v]);
+    // counting sort by degree, descending; stable in the id
+    std::vector<int64_t> start((size_t)maxd + 2, 0);
+    for (int32_t v = 0; v < n; ++v) start[(size_t)(maxd - (rp[v + 1] - rp[v])) + 1]++;
+    for (size_t d = 1; d < start.size(); ++d) start[d] += start[d - 1];
+    perm->assign((size_t)n, 0);
+    inv->assign((size_t)n, 0);
+    for (int32_t v = 0; v < n; ++v) {
+      const int64_t i = start[(size_t)(maxd - (rp[v + 1] - rp[v]))]++;
+      (*perm)[(size_t)i] = v;
+      (*inv)[(size_t)v] = (int32_t)i;
+    }
+    rp_out->assign((size_t)n + 1, 0);
+    ci_out->assign((size_t)std::max(rp[n], 1), 0);
+    int64_t w = 0;
+    for (int32_t i = 0; i < n; ++i) {
+      const int32_t v = (*perm)[(size_t)i];
+      for (int32_t e = rp[v]; e < rp[v + 1]; ++e) (*ci_out)[(size_t)w++] = (*inv)[(size_t)ci[e]];
+      (*rp_out)[(size_t)i + 1] = (int32_t)w;
+    }
+  } catch (const std::bad_alloc&) {
+    return -1;
+  }
+  return 0;
+}

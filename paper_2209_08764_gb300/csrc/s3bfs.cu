@@ -21,6 +21,12 @@ using namespace s3bfs;
 int s3bfs_host_check_duplicates(int32_t n, const int32_t* rp, const int32_t* ci, char* msg, size_t len);
 int s3bfs_host_dedup(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* rp_out,
                      std::vector<int32_t>* ci_out);
+double s3bfs_host_top_degree_share(int32_t n, const int32_t* rp, int32_t top);
+int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* perm,
+                       std::vector<int32_t>* inv, std::vector<int32_t>* rp_out, std::vector<int32_t>* ci_out);
+
+// Visited bits in shared memory cover at most this many vertices (32 KB).
+constexpr int kHubMax = 1 << 18;
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -62,6 +68,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
   }
   for (long long i = tid; i < p.max_chunks; i += stride) p.status[i].word = 0ull;
   for (long long i = tid; i < ((ctas + 3) & ~3); i += stride) p.bar_arrive[i] = 0;
+  for (long long i = tid; i < (p.hub_n >> 5); i += stride) p.hub_bits[i] = 0u;
   if (tid == 0) {
     const int rs = p.row_ptr[s], deg = p.row_ptr[s + 1] - rs;
     p.F[0][0] = s;
@@ -87,6 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
 // compact, grid barrier, per level.  Warps beyond P_l skip the level's work
 // and wait at the barrier (parked), so a small level occupies few SMs.
 __global__ void __launch_bounds__(kThreads, S3BFS_MIN_CTAS) k_level_loop(Params p) {
+  extern __shared__ uint32_t s_hub[];  // p.hub_n / 8 bytes
   const int lane = threadIdx.x & (kWarp - 1);
   const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int P = gridDim.x * kWarpsPerCta;
@@ -112,14 +120,18 @@ __global__ void __launch_bounds__(kThreads, S3BFS_MIN_CTAS) k_level_loop(Params 
       edges += e_l;
       record_level(p, l, n_l, e_l, P_l);
     }
+    // big level: take the visited-bits snapshot into shared memory
+    const int hub_lim = (p.hub_n > 0 && e_l >= p.hub_n) ? load_hub_bits(p, s_hub) : 0;
     int cnt = 0, e_begin = 0;
     if (gw < P_l) {
       const long long eb = (long long)gw * C_l;
       e_begin = (int)min(eb, (long long)e_l);
       const int e_end = (int)min(eb + C_l, (long long)e_l);
-      if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin);
+      if (e_begin < e_end)
+        cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
     }
     if (!grid_sync(p, ++bar)) break;
+    if (p.hub_n > 0) build_hub_bits(p, gw, P);
     if (P_l == 0) {
       if (gw == 0 && lane == 0) publish_empty_next(p, par);
     } else if ((int)blockIdx.x * kWarpsPerCta < P_l) {
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_explore(Params p, int l, int n_l, 
   const int e_begin = (int)min(eb, (long long)e_l);
   const int e_end = (int)min(eb + C_l, (long long)e_l);
   int cnt = 0;
-  if (e_begin < e_end) cnt = explore_chunk(p, l, l & 1, n_l, e_l, e_begin, e_end, p.cand + e_begin);
+  if (e_begin < e_end) cnt = explore_chunk(p, l, l & 1, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
   if ((threadIdx.x & (kWarp - 1)) == 0) p.cand_cnt[gw] = cnt;
 }
 
@@ -179,6 +191,22 @@ __global__ void k_check_csr(int32_t n, int32_t nnz, const int32_t* rp, const int
     if ((unsigned)ci[e] >= (unsigned)n) *bad = 2;
 }
 
+// Outputs of a renumbered graph back in the caller's vertex ids: v is the
+// caller's id, inv[v] the internal one, perm[i] the caller's id of internal i.
+__global__ void __launch_bounds__(kThreads) k_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
+                                                       const int32_t* level, const int32_t* parent,
+                                                       int32_t* level_out, int32_t* parent_out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const int i = __ldg(inv + v);
+    level_out[v] = level[i];
+    if (parent_out) {
+      const int q = parent[i];
+      parent_out[v] = q >= 0 ? __ldg(perm + q) : -1;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -196,6 +224,12 @@ struct bfs_graph {
   int debug_flags = 0;
   long long spin_ns = 1000000000ll;
   int32_t lvl_cap = 0;
+  int hub_n = 0;         // vertices [0, hub_n) have visited bits in shared memory
+  bool relabel = false;  // internal ids are degree-descending (hubs first)
+  std::vector<int32_t> h_inv;
+  int32_t *d_perm = nullptr, *d_inv = nullptr;
+  uint32_t* d_hub_bits = nullptr;
+  int32_t *d_out_level = nullptr, *d_out_parent = nullptr;  // translated outputs for host buffers
   int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr;
   int32_t *d_level = nullptr, *d_parent = nullptr;
   int32_t *d_F[2] = {nullptr, nullptr}, *d_RS[2] = {nullptr, nullptr}, *d_EX[2] = {nullptr, nullptr};
@@ -307,12 +341,6 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     g->debug_flags = opts->debug_flags;
   }
   if (!coop) g->persistent = 0;
-  int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, 0));
-  if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
-  g->ctas = per_sm * g->sms;
-  if (opts && opts->ctas > 0) g->ctas = std::min(g->ctas, (int)opts->ctas);
-  g->warps = g->ctas * kWarpsPerCta;
 
   // CSR: host data is validated / cleaned on the host, then uploaded
   std::vector<int32_t> h_rp, h_ci;
@@ -347,7 +375,58 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
       if (s3bfs_host_check_duplicates(n, rp, ci, msg, sizeof(msg)) != 0) return fail(BFS_E_MULTIGRAPH, "%s", msg);
     }
   }
-  const bool upload_from_host = !dev_in || !h_rp.empty();
+  // shared-memory visited bits: every vertex when n is small, else the
+  // kHubMax highest-degree vertices after a degree-descending renumbering,
+  // if they hold at least half of the edge endpoints (skewed graphs)
+  bool csr_on_host = !dev_in || !h_rp.empty();  // rp / ci are host arrays
+  const int relabel_opt = opts ? opts->relabel : 0;
+  if (relabel_opt >= 0) {
+    if (n <= kHubMax && relabel_opt == 0) {
+      g->hub_n = (n + 127) / 128 * 128;
+    } else {
+      std::vector<int32_t> rp_probe;
+      const int32_t* rpp = rp;
+      if (!csr_on_host) {
+        rp_probe.resize((size_t)n + 1);
+        CUDA_TRY(cudaMemcpy(rp_probe.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+        rpp = rp_probe.data();
+      }
+      if (rpp[0] != 0 || rpp[n] != nnz) return fail(BFS_E_INVAL, "row_ptr[0] must be 0 and row_ptr[n] == nnz");
+      for (int32_t v = 0; v < n; ++v)
+        if (rpp[v] > rpp[v + 1]) return fail(BFS_E_INVAL, "row_ptr decreases at %d", v);
+      const bool skewed = s3bfs_host_top_degree_share(n, rpp, kHubMax) >= 0.5;
+      if (relabel_opt == 1 || skewed) {
+        if (!csr_on_host) {
+          h_rp.swap(rp_probe);
+          h_ci.resize((size_t)std::max(nnz, 1));
+          if (nnz)
+            CUDA_TRY(cudaMemcpy(h_ci.data(), col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost));
+          rp = h_rp.data();
+          ci = h_ci.data();
+          csr_on_host = true;
+        }
+        for (int32_t e = 0; e < nnz; ++e)
+          if (ci[e] < 0 || ci[e] >= n) return fail(BFS_E_INVAL, "col_idx[%d] = %d out of range", e, ci[e]);
+        std::vector<int32_t> perm, rp2, ci2;
+        if (s3bfs_host_relabel(n, rp, ci, &perm, &g->h_inv, &rp2, &ci2) != 0)
+          return fail(BFS_E_NOMEM, "renumbering: host allocation failed");
+        h_rp.swap(rp2);
+        h_ci.swap(ci2);
+        rp = h_rp.data();
+        ci = h_ci.data();
+        g->relabel = true;
+        g->hub_n = std::min(kHubMax, (n + 127) / 128 * 128);
+        if ((rc = dalloc(g, &g->d_perm, (size_t)n)) != BFS_OK) return rc;
+        if ((rc = dalloc(g, &g->d_inv, (size_t)n)) != BFS_OK) return rc;
+        CUDA_TRY(cudaMemcpyAsync(g->d_perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                                 g->stream));
+        CUDA_TRY(cudaMemcpyAsync(g->d_inv, g->h_inv.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                                 g->stream));
+        CUDA_TRY(cudaStreamSynchronize(g->stream));
+      }
+    }
+  }
+  const bool upload_from_host = csr_on_host;
   g->n = n;
   g->nnz = nnz;
   const size_t nnz_pad = ((size_t)nnz + 3) / 4 * 4 + 4;
@@ -358,7 +437,20 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   CUDA_TRY(cudaMemsetAsync(g->d_col_idx, 0, sizeof(int32_t) * nnz_pad, g->stream));
   if (nnz) CUDA_TRY(cudaMemcpyAsync(g->d_col_idx, ci, sizeof(int32_t) * (size_t)nnz, kind, g->stream));
 
+  // persistent grid: every CTA that fits next to the shared-memory bits
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, (size_t)g->hub_n / 8));
+  if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
+  g->ctas = per_sm * g->sms;
+  if (opts && opts->ctas > 0) g->ctas = std::min(g->ctas, (int)opts->ctas);
+  g->warps = g->ctas * kWarpsPerCta;
+
   // work memory
+  if (g->hub_n > 0 && (rc = dalloc(g, &g->d_hub_bits, (size_t)g->hub_n / 32)) != BFS_OK) return rc;
+  if (g->relabel) {
+    if ((rc = dalloc(g, &g->d_out_level, (size_t)n)) != BFS_OK) return rc;
+    if ((rc = dalloc(g, &g->d_out_parent, (size_t)n)) != BFS_OK) return rc;
+  }
   g->lvl_cap = (int32_t)std::min<long long>((long long)n + 1, 1 << 20);
   const int max_chunks = g->warps;
   if ((rc = dalloc(g, &g->d_level, (size_t)n + 4)) != BFS_OK) return rc;
@@ -453,6 +545,8 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.max_chunks = g->warps;
   p.debug_flags = g->debug_flags;
   p.spin_ns = g->spin_ns;
+  p.hub_bits = g->d_hub_bits;
+  p.hub_n = g->persistent ? g->hub_n : 0;
   return p;
 }
 
@@ -466,8 +560,8 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
   if (g->persistent) {
     Params pc = p;
     void* args[] = {&pc};
-    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(g->ctas), dim3(kThreads), args, 0,
-                                         g->stream));
+    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(g->ctas), dim3(kThreads), args,
+                                         (size_t)p.hub_n / 8, g->stream));
   } else {
     // launch per phase; the host reads n and e of every level
     LevelCtrl* hc = reinterpret_cast<LevelCtrl*>(g->h_ctrl);
@@ -569,16 +663,28 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
 static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* parent_out, bfs_stats* stats) {
   const bool lvl_dev = is_device_ptr(level_out);
   const bool par_dev = parent_out && is_device_ptr(parent_out);
-  int32_t* level = lvl_dev ? level_out : g->d_level;
-  int32_t* parent = par_dev ? parent_out : g->d_parent;
-  const Params p = make_params(g, src, level, parent);
+  // without renumbering the kernels write device outputs in place
+  int32_t* level = (lvl_dev && !g->relabel) ? level_out : g->d_level;
+  int32_t* parent = (par_dev && !g->relabel) ? parent_out : g->d_parent;
+  const Params p = make_params(g, g->relabel ? g->h_inv[src] : src, level, parent);
   const bool timed = stats != nullptr;
   int rc = enqueue_traversal(g, p, timed);
   if (rc != BFS_OK) return rc;
+  const int32_t* lvl_src = level;
+  const int32_t* par_src = parent;
+  if (g->relabel) {
+    int32_t* lo = lvl_dev ? level_out : g->d_out_level;
+    int32_t* po = parent_out ? (par_dev ? parent_out : g->d_out_parent) : nullptr;
+    const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
+    k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, level, parent, lo, po);
+    CUDA_TRY(cudaGetLastError());
+    lvl_src = lo;
+    par_src = po;
+  }
   if (!lvl_dev)
-    CUDA_TRY(cudaMemcpyAsync(level_out, level, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(level_out, lvl_src, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
   if (parent_out && !par_dev)
-    CUDA_TRY(cudaMemcpyAsync(parent_out, parent, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost,
+    CUDA_TRY(cudaMemcpyAsync(parent_out, par_src, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost,
                              g->stream));
   return finish_traversal(g, stats, timed, src);
 }
@@ -751,6 +857,8 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   p.max_chunks = d->ctas * kWarpsPerCta;
   p.debug_flags = 0;
   p.spin_ns = 1000000000ll;
+  p.hub_bits = nullptr;
+  p.hub_n = 0;
 
   // k_init clears the look-back and barrier state left by the previous call
   const int igrid = std::max(1, std::min(d->sms * 8, (int)(((long long)n / 4 + 255) / 256)));

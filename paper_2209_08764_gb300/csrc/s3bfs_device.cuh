@@ -111,6 +111,11 @@ struct Params {
   int32_t max_chunks;   // size of status / cand_cnt
   int32_t debug_flags;
   long long spin_ns;
+  // visited bits of vertices [0, hub_n) (hub_n a multiple of 128, 0 = none):
+  // rebuilt from level[] after every level's explore, copied to shared memory
+  // at the start of a level with at least hub_n edges
+  uint32_t* hub_bits;
+  int32_t hub_n;
 };
 
 // ---------------------------------------------------------------------------
@@ -162,6 +167,11 @@ __device__ __forceinline__ int4 ld_nc4(const int4* p) {
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 ld_cg4u(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.cg.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
   return v;
 }
 __device__ __forceinline__ int4 ld_relaxed4(const int4* p) {
@@ -329,8 +339,11 @@ __device__ __forceinline__ int emit(int2* out, int cnt, bool k, int v, int u, in
 }
 
 // Returns the number of candidate pairs written to out (warp-uniform).
+// s_hub / hub_lim: visited bits of vertices [0, hub_lim) in shared memory, a
+// snapshot taken at the start of the level (hub_lim = 0: none).  A set bit
+// means the vertex already has a level, so its level[] test is skipped.
 __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, int e_begin, int e_end,
-                             int2* out) {
+                             int2* out, const uint32_t* s_hub, int hub_lim) {
   const int lane = threadIdx.x & (kWarp - 1);
   // (selects, not p.EX[par]: a runtime index into the parameter block would
   // copy it to local memory)
@@ -417,7 +430,8 @@ __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, 
         const int cc[4] = {c[r].x, c[r].y, c[r].z, c[r].w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          vv[r][j] = pos[r] + j >= wp0[r] && pos[r] + j < wp1[r];
+          const bool known = cc[j] < hub_lim && ((s_hub[cc[j] >> 5] >> (cc[j] & 31)) & 1u);
+          vv[r][j] = pos[r] + j >= wp0[r] && pos[r] + j < wp1[r] && !known;
           lv[r][j] = vv[r][j] ? ld_level(level + cc[j]) : 0;
         }
       }
@@ -648,6 +662,28 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
     }
   }
   return true;
+}
+
+// Visited bits of vertices [0, hub_n), one warp per 32-vertex word, from the
+// level array after a level's explore (all its level stores are visible).
+__device__ __forceinline__ void build_hub_bits(const Params& p, int gw, int P) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int words = p.hub_n >> 5;
+  for (int w = gw; w < words; w += P) {
+    const int lv = ld_relaxed_nb(p.level + (w << 5) + lane);
+    const unsigned m = __ballot_sync(kFull, lv >= 0);
+    if (lane == 0) p.hub_bits[w] = m;
+  }
+}
+
+// Copies the visited bits into shared memory (whole CTA); returns hub_n.
+__device__ __forceinline__ int load_hub_bits(const Params& p, uint32_t* s_hub) {
+  const int q = p.hub_n >> 7;
+  const uint4* src = reinterpret_cast<const uint4*>(p.hub_bits);
+  uint4* dst = reinterpret_cast<uint4*>(s_hub);
+  for (int i = threadIdx.x; i < q; i += blockDim.x) dst[i] = ld_cg4u(src + i);
+  __syncthreads();
+  return p.hub_n;
 }
 
 __device__ __forceinline__ void publish_empty_next(const Params& p, int par) {

@@ -51,8 +51,8 @@ def test_host_only_calls(lib):
 
 
 def test_struct_layout_matches_header():
-    # int32 x 6
-    assert ctypes.sizeof(B.bfs_opts) == 24
+    # int32 x 7
+    assert ctypes.sizeof(B.bfs_opts) == 28
     # 2 int32, 3 int64, 2 float, pointer, int32 (+ padding)
     assert B.bfs_stats.per_level.offset == 40
     assert ctypes.sizeof(B.bfs_stats) == 56

@@ -44,10 +44,11 @@ def _named_graphs():
     return g
 
 
+@pytest.mark.parametrize("relabel", [0, 1, -1])
 @pytest.mark.parametrize("name", sorted(_named_graphs()))
-def test_named_graphs(name):
+def test_named_graphs(name, relabel):
     rp, ci = _named_graphs()[name]
-    d = Dev(rp, ci)
+    d = Dev(rp, ci, relabel=relabel) if relabel else Dev(rp, ci)
     try:
         n = len(rp) - 1
         srcs = sorted({0, n // 2, n - 1})
@@ -65,13 +66,14 @@ def _directed_csr(n, edges):
     return np.cumsum(rp).astype(np.int32), np.array([v for _, v in edges], np.int32)
 
 
-def test_directed_with_zero_outdegree_frontier():
+@pytest.mark.parametrize("relabel", [0, 1])
+def test_directed_with_zero_outdegree_frontier(relabel):
     rng = np.random.default_rng(5)
     n = 3000
     e = [(int(a), int(b)) for a, b in rng.integers(0, n, size=(9000, 2)) if a != b]
     e += [(0, v) for v in range(1, 200)]           # a hub whose neighbours mostly have out-degree 0
     rp, ci = _directed_csr(n, e)
-    d = Dev(rp, ci)
+    d = Dev(rp, ci, relabel=relabel) if relabel else Dev(rp, ci)
     try:
         for s in (0, 1, 17, 2999):
             check_against_oracle(d, s)
@@ -100,7 +102,8 @@ def test_rmat16_64_sources(rmat16):
     dict(chunk_edges=1), dict(chunk_edges=2), dict(chunk_edges=3), dict(chunk_edges=31), dict(chunk_edges=32),
     dict(chunk_edges=33), dict(chunk_edges=4096), dict(ctas=1), dict(ctas=3), dict(ctas=5, chunk_edges=7),
     dict(persistent=-1), dict(persistent=-1, chunk_edges=5), dict(work_insensitive=1),
-    dict(work_insensitive=1, ctas=2),
+    dict(work_insensitive=1, ctas=2), dict(relabel=1), dict(relabel=-1), dict(relabel=1, chunk_edges=1, ctas=7),
+    dict(relabel=1, persistent=-1), dict(relabel=1, work_insensitive=1),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_rmat16_launch_configurations(rmat16, opts):
     rp, ci, srcs, keys = rmat16
@@ -144,9 +147,10 @@ def test_repeated_runs_race_stress(rmat16):
         d.close()
 
 
-def test_host_outputs_and_no_parent(rmat16):
+@pytest.mark.parametrize("relabel", [0, 1])
+def test_host_outputs_and_no_parent(rmat16, relabel):
     rp, ci, srcs, keys = rmat16
-    d = Dev(rp, ci)
+    d = Dev(rp, ci, relabel=relabel) if relabel else Dev(rp, ci)
     try:
         s = int(srcs[2])
         want, _ = oracle.bfs(rp, ci, s)
@@ -165,10 +169,11 @@ def test_host_outputs_and_no_parent(rmat16):
         d.close()
 
 
-def test_unaligned_device_outputs(rmat16):
+@pytest.mark.parametrize("relabel", [0, 1])
+def test_unaligned_device_outputs(rmat16, relabel):
     import torch
     rp, ci, srcs, keys = rmat16
-    d = Dev(rp, ci)
+    d = Dev(rp, ci, relabel=relabel) if relabel else Dev(rp, ci)
     try:
         s = int(srcs[3])
         want, _ = oracle.bfs(rp, ci, s)
@@ -181,10 +186,11 @@ def test_unaligned_device_outputs(rmat16):
         d.close()
 
 
-def test_run_batch_matches_single_runs(rmat16):
+@pytest.mark.parametrize("relabel", [0, 1])
+def test_run_batch_matches_single_runs(rmat16, relabel):
     import torch
     rp, ci, srcs, keys = rmat16
-    d = Dev(rp, ci)
+    d = Dev(rp, ci, relabel=relabel) if relabel else Dev(rp, ci)
     try:
         k = 16
         S = np.ascontiguousarray(srcs[:k])
@@ -271,13 +277,14 @@ def test_multigraph_rejected_or_deduplicated():
         d.close()
 
 
-def test_device_pointer_input():
+@pytest.mark.parametrize("relabel", [0, 1, -1])
+def test_device_pointer_input(relabel):
     import torch
     rp, ci = graphgen.rmat(12, 16, seed=3)
     drp = torch.from_numpy(rp).cuda()
     dci = torch.from_numpy(ci).cuda()
     g = B.bfs_create_csr(len(rp) - 1, len(ci), drp, dci, B.BFS_DEVICE_PTRS,
-                         None, torch.cuda.current_stream().cuda_stream)
+                         make_opts(relabel=relabel), torch.cuda.current_stream().cuda_stream)
     try:
         del drp, dci
         torch.cuda.synchronize()
