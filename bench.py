@@ -338,7 +338,7 @@ def main():
         B.bfs_run(g, int(srcs[0]), level, parent, st2)
         L = min(st2.num_levels, cap)
         rows = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS)
-        per_level = {"src": int(srcs[0]), "fields": ["n_l", "e_l", "c_l", "active_warps", "active_sms", "ns"],
+        per_level = {"src": int(srcs[0]), "fields": ["n_l", "e_l", "c_l", "active_warps", "active_sms", "ns", "ns_explore"],
                      "rows": rows.tolist() if L <= 64 else rows[:64].tolist(), "levels": L,
                      "ns_total": int(rows[:, 5].sum())}
     if args.dump and rank == 0:

@@ -48,7 +48,7 @@ typedef struct bfs_opts {
                                P_l = min(P, ceil(e_l / chunk_edges)) warps, the
                                work-sensitive count of Fig. 1 lines 11/16 (the
                                paper's own formula is chunk_edges = 1).  Default 64 */
-  int32_t ctas;             /* persistent grid size G (CTAs of 256 threads); 0 = every
+  int32_t ctas;             /* persistent grid size G (CTAs of 1024 threads); 0 = every
                                CTA that can be co-resident on the device */
   int32_t persistent;       /* 1 (default): one cooperative launch runs all levels,
                                separated by device grid barriers; -1: one launch per
@@ -67,14 +67,15 @@ typedef struct bfs_opts {
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */
-#define BFS_LEVEL_FIELDS 6
+#define BFS_LEVEL_FIELDS 7
 /* [0] n_l          frontier size (vertices at distance l)
  * [1] e_l          edges the level scans (sum of frontier out-degrees)
  * [2] c_l          candidates emitted by the explore step (n_{l+1} <= c_l <= e_l)
  * [3] active_warps P_l, warps that explored this level
  * [4] active_sms   distinct SMs hosting those warps (-1 with one launch per phase)
  * [5] ns           device time of the level, explore to the end of the compact
- *                  barrier, from the global timer (-1 with one launch per phase) */
+ *                  barrier, from the global timer (-1 with one launch per phase)
+ * [6] ns_explore   the part of [5] up to the end of the explore barrier */
 
 /* Statistics of one traversal (all optional). */
 typedef struct bfs_stats {

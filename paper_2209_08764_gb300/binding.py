@@ -27,7 +27,7 @@ BFS_VALIDATE = 2
 BFS_DEDUP = 4
 
 BFS_DEBUG_STALL_BARRIER = 1
-BFS_LEVEL_FIELDS = 6
+BFS_LEVEL_FIELDS = 7
 
 EXPORTS = ("bfs_create_csr", "bfs_run", "bfs_run_batch", "bfs_destroy", "bfs_strerror", "bfs_last_error",
            "bfs_graph_info", "bfs_run_csr_noalloc")

@@ -25,8 +25,8 @@ double s3bfs_host_top_degree_share(int32_t n, const int32_t* rp, int32_t top);
 int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* perm,
                        std::vector<int32_t>* inv, std::vector<int32_t>* rp_out, std::vector<int32_t>* ci_out);
 
-// Visited bits in shared memory cover at most this many vertices (32 KB).
-constexpr int kHubMax = 1 << 18;
+// dynamic shared memory of the level loop: the visited bits
+static size_t loop_smem(int hub_n) { return (size_t)hub_n / 8; }
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
 // compact, grid barrier, per level.  Warps beyond P_l skip the level's work
 // and wait at the barrier (parked), so a small level occupies few SMs.
 __global__ void __launch_bounds__(kThreads, S3BFS_MIN_CTAS) k_level_loop(Params p) {
-  extern __shared__ uint32_t s_hub[];  // p.hub_n / 8 bytes
+  extern __shared__ __align__(16) uint32_t s_hub[];  // visited bits, p.hub_n / 8 bytes
   const int lane = threadIdx.x & (kWarp - 1);
   const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int P = gridDim.x * kWarpsPerCta;
@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(kThreads, S3BFS_MIN_CTAS) k_level_loop(Params 
         cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
     }
     if (!grid_sync(p, ++bar)) break;
+    if (leader && l < p.lvl_cap)
+      p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
     if (p.hub_n > 0) build_hub_bits(p, gw, P);
     if (P_l == 0) {
       if (gw == 0 && lane == 0) publish_empty_next(p, par);
@@ -438,8 +440,9 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   if (nnz) CUDA_TRY(cudaMemcpyAsync(g->d_col_idx, ci, sizeof(int32_t) * (size_t)nnz, kind, g->stream));
 
   // persistent grid: every CTA that fits next to the shared-memory bits
+  CUDA_TRY(cudaFuncSetAttribute(k_level_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(g->hub_n)));
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, (size_t)g->hub_n / 8));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, loop_smem(g->hub_n)));
   if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
   g->ctas = per_sm * g->sms;
   if (opts && opts->ctas > 0) g->ctas = std::min(g->ctas, (int)opts->ctas);
@@ -561,7 +564,7 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
     Params pc = p;
     void* args[] = {&pc};
     CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(g->ctas), dim3(kThreads), args,
-                                         (size_t)p.hub_n / 8, g->stream));
+                                         loop_smem(p.hub_n), g->stream));
   } else {
     // launch per phase; the host reads n and e of every level
     LevelCtrl* hc = reinterpret_cast<LevelCtrl*>(g->h_ctrl);
@@ -654,7 +657,7 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
       int32_t* r = stats->per_level + (size_t)l * kLevelFields;
       const int ctas = std::min(g->ctas, (r[3] + kWarpsPerCta - 1) / kWarpsPerCta);
       r[4] = g->persistent ? distinct[ctas] : -1;
-      if (!g->persistent) r[5] = -1;
+      if (!g->persistent) r[5] = r[6] = -1;
     }
   }
   return BFS_OK;
@@ -783,7 +786,7 @@ static int noalloc_setup(int dev, NoAllocDevice** out) {
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return fail(BFS_E_CUDA, "device %d has no cooperative launch", dev);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, loop_smem(0)));
     if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
     d.scratch = static_cast<unsigned char*>(ptr);
     d.sms = sms;
@@ -865,7 +868,8 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   k_init<<<igrid, kThreads, 0, stream>>>(p, d->ctas);
   CUDA_TRY(cudaGetLastError());
   void* args[] = {&p};
-  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(d->ctas), dim3(kThreads), args, 0, stream));
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(d->ctas), dim3(kThreads), args, loop_smem(0),
+                                       stream));
   DevState h;
   CUDA_TRY(cudaMemcpyAsync(&h, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
