@@ -200,6 +200,81 @@ def cpu_baseline(w, rp, ci, srcs, budget_s):
             "sample": f"first {k} of the {len(srcs)} sources, one traversal each ({t:.1f} s)"}
 
 
+def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev):
+    """One step = one bfs_run_batch over all sources (groups of 64 share a
+    bitmask traversal); compared with the same sources run one at a time."""
+    n, nnz = len(rp) - 1, len(ci)
+    k = len(srcs)
+    stream = torch.cuda.current_stream()
+    g = B.bfs_create_csr(n, nnz, rp, ci, B.BFS_VALIDATE | B.BFS_SYMMETRIC, None, stream.cuda_stream)
+    L = torch.empty(k * n, dtype=torch.int32, device=dev)
+    P = None if args.no_parents else torch.empty(k * n, dtype=torch.int32, device=dev)
+    S = np.ascontiguousarray(srcs, np.int32)
+    st = (B.bfs_stats * k)()
+    for _ in range(args.warmup):
+        B.bfs_run_batch(g, S, k, L, P, None)
+    B.bfs_run_batch(g, S, k, L, P, st)
+    deg = np.diff(rp.astype(np.int64))
+    Lh = L.cpu().numpy().reshape(k, n)
+    teps = [int(deg[Lh[i] >= 0].sum() // 2) for i in range(k)]
+    edges_per_step = sum(teps)
+    levels = max(st[i].num_levels for i in range(k))
+    work = st[0].work_edges
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms_kernel = []
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            B.bfs_run_batch(g, S, k, L, P, st)
+            ms_kernel.append(st[0].ms_level_step)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    gteps = edges_per_step * args.steps * ws / (ms_max / 1e3) / 1e9
+    # the same sources one at a time through bfs_run (single-source S3BFS)
+    lv = torch.empty(n, dtype=torch.int32, device=dev)
+    pa = torch.empty(n, dtype=torch.int32, device=dev)
+    for s in S[:2]:
+        B.bfs_run(g, int(s), lv, pa, None)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in S:
+        B.bfs_run(g, int(s), lv, pa, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_gteps = edges_per_step / (e0.elapsed_time(e1) / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    kms = float(np.mean(ms_kernel))
+    bytes_launch = 12.0 * work + 24.0 * n * levels
+    achieved = bytes_launch / (kms / 1e3) / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": dict(config_of(args.workload, w, rp, ci), mode="batch-bitmask", k=k,
+                               parents=not args.no_parents),
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                             "kernel": "k_msbfs", "algorithmic_bytes_per_launch": bytes_launch,
+                             "avg_launch_ms": kms, "model": "12 B per pulled edge + 24 B per vertex per level"},
+                "clocks": clk.summary(), "gpu_launches": int(args.steps * (k + 63) // 64 * 3),
+                "sequential_gteps": round(seq_gteps, 3), "batch_speedup": round(gteps / seq_gteps, 2),
+                "levels": levels, "pulled_edges": int(work)}
+        print(json.dumps(line), flush=True)
+    B.bfs_destroy(g)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,6 +294,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dump", default="", help="write per-traversal records of the timed steps (JSON) here")
     ap.add_argument("--levels", action="store_true", help="add the per-level statistics of the first source")
+    ap.add_argument("--batch", action="store_true",
+                    help="all sources of a step in one bfs_run_batch call (64-source bitmask traversal)")
+    ap.add_argument("--no-parents", action="store_true", help="levels only (batch mode)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.sources:
@@ -244,6 +322,9 @@ def main():
     rp, ci = make_graph(w)
     n, nnz = len(rp) - 1, len(ci)
     srcs = sources_for(w, rp, rank)
+    if args.batch:
+        run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev)
+        return
     deg = np.diff(rp.astype(np.int64))
     stream = torch.cuda.current_stream()
     opts = B.bfs_opts()

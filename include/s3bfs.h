@@ -37,6 +37,8 @@ extern "C" {
 #define BFS_DEVICE_PTRS 1 /* row_ptr / col_idx are device pointers (else host pointers) */
 #define BFS_VALIDATE 2    /* check the CSR on the host before use (see bfs_create_csr) */
 #define BFS_DEDUP 4       /* sort every row and drop duplicate neighbours and self-loops */
+#define BFS_SYMMETRIC 8   /* every edge has its reverse (an undirected graph); checked with
+                             BFS_VALIDATE.  Enables the bitmask path of bfs_run_batch */
 
 /* ---- bfs_opts.debug_flags (tests only) --------------------------------- */
 #define BFS_DEBUG_STALL_BARRIER 1 /* the last CTA never arrives at the first grid barrier,
@@ -64,6 +66,9 @@ typedef struct bfs_opts {
                                they hold >= half of the edge endpoints; 1 = always
                                renumber; -1 = neither.  Renumbering is internal:
                                inputs and outputs keep the caller's vertex ids */
+  int32_t batch_bitmask;    /* bfs_run_batch on a BFS_SYMMETRIC graph: 0 (default) =
+                               groups of up to 64 sources share one traversal with a
+                               64-bit mask per vertex; -1 = one traversal per source */
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */
@@ -88,6 +93,8 @@ typedef struct bfs_stats {
   float ms_total;         /* device time including initialisation */
   int32_t *per_level;     /* in: optional host buffer of per_level_cap * BFS_LEVEL_FIELDS int32 */
   int32_t per_level_cap;  /* in: capacity in levels; levels beyond it are counted, not recorded */
+  int64_t work_edges;     /* neighbour entries the kernels read: edges_scanned for one source;
+                             for a bitmask batch group, the pulled entries of all its levels */
 } bfs_stats;
 
 typedef struct bfs_graph bfs_graph; /* opaque; owned by the library */
@@ -146,8 +153,21 @@ int bfs_run(bfs_graph *g, int32_t src, int32_t *level_out, int32_t *parent_out, 
  *
  * levels_out[k*n] (source-major: traversal i at levels_out + i*n), and
  * parents_out[k*n] (nullable), device or host pointers as for bfs_run.  stats
- * (nullable) points to k records.  Same semantics and errors as k calls of
- * bfs_run; on error the index of the failing source is in bfs_last_error().
+ * (nullable) points to k records.  Results are those of k calls of bfs_run
+ * (levels identical; parents a valid BFS tree, not necessarily the same one).
+ *
+ * On a graph created with BFS_SYMMETRIC (and opts.batch_bitmask = 0) the
+ * sources are taken 64 at a time in one launch: every vertex keeps a 64-bit
+ * mask of the sources that reached it and pulls its neighbours' frontier
+ * masks each level (multi-source BFS; not in the paper, whose distance
+ * definition it keeps).  Its working memory (3 x 8 bytes per vertex, plus
+ * 2 x 64 x n int32 for host output buffers) is allocated at the first such
+ * call.  In each stats record of such a group, ms_level_step and ms_total are
+ * those of the whole group and candidates = reached - 1.  Otherwise the
+ * sources run one after another.
+ *
+ * Errors as for bfs_run; on error the index of the failing source (or group)
+ * is in bfs_last_error().
  */
 int bfs_run_batch(bfs_graph *g, const int32_t *srcs, int32_t k, int32_t *levels_out, int32_t *parents_out,
                   bfs_stats *stats);

@@ -8,7 +8,7 @@ used only for device memory and the current stream.
 from __future__ import annotations
 
 from .binding import (BFS_DEBUG_STALL_BARRIER, BFS_DEDUP, BFS_DEVICE_PTRS, BFS_E_CUDA, BFS_E_INVAL,  # noqa: F401
-                      BFS_E_MULTIGRAPH, BFS_E_NOMEM, BFS_E_TIMEOUT, BFS_LEVEL_FIELDS, BFS_OK, BFS_VALIDATE,
+                      BFS_E_MULTIGRAPH, BFS_E_NOMEM, BFS_E_TIMEOUT, BFS_LEVEL_FIELDS, BFS_OK, BFS_SYMMETRIC, BFS_VALIDATE,
                       BFSError, bfs_create_csr, bfs_destroy, bfs_graph_info, bfs_last_error, bfs_opts, bfs_run,
                       bfs_run_batch, bfs_stats, bfs_strerror)
 

@@ -25,6 +25,7 @@ BFS_E_TIMEOUT = -5
 BFS_DEVICE_PTRS = 1
 BFS_VALIDATE = 2
 BFS_DEDUP = 4
+BFS_SYMMETRIC = 8
 
 BFS_DEBUG_STALL_BARRIER = 1
 BFS_LEVEL_FIELDS = 7
@@ -42,6 +43,7 @@ class bfs_opts(ctypes.Structure):
         ("spin_limit_ms", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
         ("relabel", ctypes.c_int32),
+        ("batch_bitmask", ctypes.c_int32),
     ]
 
 
@@ -56,6 +58,7 @@ class bfs_stats(ctypes.Structure):
         ("ms_total", ctypes.c_float),
         ("per_level", ctypes.POINTER(ctypes.c_int32)),
         ("per_level_cap", ctypes.c_int32),
+        ("work_edges", ctypes.c_int64),
     ]
 
 

@@ -112,3 +112,16 @@ int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vec
   }
   return 0;
 }
+
+// True if every edge (u, v) has its reverse (v, u).  Rows are sorted in a
+// copy where needed, then every reverse edge is found by binary search.
+int s3bfs_host_is_symmetric(int32_t n, const int32_t* rp, const int32_t* ci) {
+  std::vector<int32_t> sorted(ci, ci + rp[n]);
+  for (int32_t u = 0; u < n; ++u) std::sort(sorted.begin() + rp[u], sorted.begin() + rp[u + 1]);
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
+      const int32_t v = sorted[(size_t)e];
+      if (!std::binary_search(sorted.begin() + rp[v], sorted.begin() + rp[v + 1], u)) return 0;
+    }
+  return 1;
+}

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "msbfs.cuh"
 #include "s3bfs.h"
 #include "s3bfs_device.cuh"
 
@@ -22,6 +23,7 @@ int s3bfs_host_check_duplicates(int32_t n, const int32_t* rp, const int32_t* ci,
 int s3bfs_host_dedup(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* rp_out,
                      std::vector<int32_t>* ci_out);
 double s3bfs_host_top_degree_share(int32_t n, const int32_t* rp, int32_t top);
+int s3bfs_host_is_symmetric(int32_t n, const int32_t* rp, const int32_t* ci);
 int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* perm,
                        std::vector<int32_t>* inv, std::vector<int32_t>* rp_out, std::vector<int32_t>* ci_out);
 
@@ -247,6 +249,20 @@ struct bfs_graph {
   int32_t* h_ctrl = nullptr; // pinned, launch-per-phase mode
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
+  // multi-source (bitmask) batches, allocated at the first batch
+  bool symmetric = false;
+  int batch_bitmask = 0;
+  bool ms_ready = false;
+  int ms_ctas = 0;
+  unsigned long long *d_seen = nullptr, *d_fr[2] = {nullptr, nullptr};
+  int32_t *d_heavy = nullptr, *d_huge = nullptr;
+  int32_t n_heavy = 0, n_huge = 0;
+  unsigned long long *d_block_or = nullptr, *d_level_bits = nullptr;
+  long long* d_block_edges = nullptr;
+  long long* d_counts = nullptr;
+  int32_t* d_groups = nullptr;  // vs[64], src_int[64], src_out[64]
+  unsigned long long* d_masks = nullptr;
+  int32_t *d_stage_level = nullptr, *d_stage_parent = nullptr;  // 64 x n, for host outputs
 };
 
 static thread_local char g_last_error[512] = "";
@@ -341,7 +357,9 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     g->work_insensitive = opts->work_insensitive != 0;
     if (opts->spin_limit_ms > 0) g->spin_ns = (long long)opts->spin_limit_ms * 1000000ll;
     g->debug_flags = opts->debug_flags;
+    g->batch_bitmask = opts->batch_bitmask;
   }
+  g->symmetric = (flags & BFS_SYMMETRIC) != 0;
   if (!coop) g->persistent = 0;
 
   // CSR: host data is validated / cleaned on the host, then uploaded
@@ -376,6 +394,8 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
       char msg[256];
       if (s3bfs_host_check_duplicates(n, rp, ci, msg, sizeof(msg)) != 0) return fail(BFS_E_MULTIGRAPH, "%s", msg);
     }
+    if ((flags & BFS_SYMMETRIC) && !s3bfs_host_is_symmetric(n, rp, ci))
+      return fail(BFS_E_INVAL, "BFS_SYMMETRIC: an edge lacks its reverse");
   }
   // shared-memory visited bits: every vertex when n is small, else the
   // kHubMax highest-degree vertices after a degree-descending renumbering,
@@ -503,7 +523,8 @@ extern "C" int bfs_create_csr(int32_t n, int32_t nnz, const int32_t* row_ptr, co
   if (n < 1 || n > 0x7FFFFFFF - 8) return fail(BFS_E_INVAL, "n = %d out of range [1, 2^31-8)", n);
   if (nnz < 0 || nnz > 0x7FFFFFFF - 64) return fail(BFS_E_INVAL, "nnz = %d out of range", nnz);
   if (!row_ptr || (nnz > 0 && !col_idx)) return fail(BFS_E_INVAL, "NULL CSR array");
-  if (flags & ~(BFS_DEVICE_PTRS | BFS_VALIDATE | BFS_DEDUP)) return fail(BFS_E_INVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(BFS_DEVICE_PTRS | BFS_VALIDATE | BFS_DEDUP | BFS_SYMMETRIC))
+    return fail(BFS_E_INVAL, "unknown flags 0x%x", flags);
   bfs_graph* g = new (std::nothrow) bfs_graph();
   if (!g) return fail(BFS_E_NOMEM, "host allocation failed");
   g->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -630,6 +651,7 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
   stats->candidates = st.cands;
   stats->ms_level_step = 0.f;
   stats->ms_total = 0.f;
+  stats->work_edges = st.edges;
   if (timed) {
     CUDA_TRY(cudaEventElapsedTime(&stats->ms_level_step, g->ev[1], g->ev[2]));
     CUDA_TRY(cudaEventElapsedTime(&stats->ms_total, g->ev[0], g->ev[2]));
@@ -704,6 +726,170 @@ extern "C" int bfs_run(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* p
   return rc;
 }
 
+// ---- multi-source batches (bitmask frontiers) -----------------------------
+
+static int ms_setup(bfs_graph* g) {
+  if (g->ms_ready) return BFS_OK;
+  int rc;
+  const size_t n = (size_t)g->n;
+  if ((rc = dalloc(g, &g->d_seen, n)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_fr[0], n)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_fr[1], n)) != BFS_OK) return rc;
+  // heavy vertices (internal ids), from a host copy of row_ptr
+  std::vector<int32_t> rp(n + 1), heavy, huge;
+  CUDA_TRY(cudaMemcpy(rp.data(), g->d_row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+  for (size_t v = 0; v < n; ++v) {
+    const int32_t d = rp[v + 1] - rp[v];
+    if (d > kMsHuge)
+      huge.push_back((int32_t)v);
+    else if (d > kMsHeavy)
+      heavy.push_back((int32_t)v);
+  }
+  g->n_heavy = (int32_t)heavy.size();
+  g->n_huge = (int32_t)huge.size();
+  if ((rc = dalloc(g, &g->d_heavy, std::max<size_t>(heavy.size(), 1))) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_huge, std::max<size_t>(huge.size(), 1))) != BFS_OK) return rc;
+  if (!heavy.empty())
+    CUDA_TRY(cudaMemcpy(g->d_heavy, heavy.data(), sizeof(int32_t) * heavy.size(), cudaMemcpyHostToDevice));
+  if (!huge.empty())
+    CUDA_TRY(cudaMemcpy(g->d_huge, huge.data(), sizeof(int32_t) * huge.size(), cudaMemcpyHostToDevice));
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs, kThreads, 0));
+  if (per_sm < 1) return fail(BFS_E_CUDA, "multi-source kernel cannot be resident (occupancy 0)");
+  g->ms_ctas = per_sm * g->sms;
+  if ((rc = dalloc(g, &g->d_block_or, 2 * (size_t)g->ms_ctas)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_level_bits, (size_t)g->lvl_cap)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_counts, (size_t)g->ms_ctas * 128)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_block_edges, (size_t)g->ms_ctas)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_groups, 3 * 64)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_masks, 64)) != BFS_OK) return rc;
+  if (g->ctas < g->ms_ctas) {
+    // the barrier's arrival words must cover this grid too
+    if ((rc = dalloc(g, &g->d_arrive, (size_t)(g->ms_ctas + 3) / 4 * 4)) != BFS_OK) return rc;
+  }
+  g->ms_ready = true;
+  return BFS_OK;
+}
+
+// Up to 64 sources in one launch; outputs as for bfs_run_batch.
+static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* levels_out, int32_t* parents_out,
+                             bfs_stats* stats) {
+  const size_t n = (size_t)g->n;
+  const bool lvl_dev = is_device_ptr(levels_out);
+  const bool par_dev = parents_out && is_device_ptr(parents_out);
+  int rc;
+  if ((!lvl_dev && !g->d_stage_level) && (rc = dalloc(g, &g->d_stage_level, 64 * n)) != BFS_OK) return rc;
+  if (parents_out && !par_dev && !g->d_stage_parent && (rc = dalloc(g, &g->d_stage_parent, 64 * n)) != BFS_OK)
+    return rc;
+  int32_t* L = lvl_dev ? levels_out : g->d_stage_level;
+  int32_t* Pp = parents_out ? (par_dev ? parents_out : g->d_stage_parent) : nullptr;
+  // sources grouped by (internal) vertex
+  int32_t vs[64], src_int[64], src_out[64];
+  unsigned long long masks[64];
+  int groups = 0;
+  for (int i = 0; i < k; ++i) {
+    src_out[i] = srcs[i];
+    src_int[i] = g->relabel ? g->h_inv[srcs[i]] : srcs[i];
+    int j = 0;
+    while (j < groups && vs[j] != src_int[i]) ++j;
+    if (j == groups) {
+      vs[groups] = src_int[i];
+      masks[groups++] = 0;
+    }
+    masks[j] |= 1ull << i;
+  }
+  int32_t hg[3 * 64];
+  memcpy(hg, vs, sizeof(vs));
+  memcpy(hg + 64, src_int, sizeof(src_int));
+  memcpy(hg + 128, src_out, sizeof(src_out));
+  CUDA_TRY(cudaMemcpyAsync(g->d_groups, hg, sizeof(hg), cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(g->d_masks, masks, sizeof(masks), cudaMemcpyHostToDevice, g->stream));
+  MsParams p;
+  memset(&p, 0, sizeof(p));
+  p.n = g->n;
+  p.k = k;
+  p.row_ptr = g->d_row_ptr;
+  p.col_idx = g->d_col_idx;
+  p.seen = g->d_seen;
+  p.fr[0] = g->d_fr[0];
+  p.fr[1] = g->d_fr[1];
+  p.heavy = g->d_heavy;
+  p.n_heavy = g->n_heavy;
+  p.huge = g->d_huge;
+  p.n_huge = g->n_huge;
+  p.levels_out = L;
+  p.parents_out = Pp;
+  p.perm = g->relabel ? g->d_perm : nullptr;
+  p.block_or = g->d_block_or;
+  p.level_bits = g->d_level_bits;
+  p.block_edges = g->d_block_edges;
+  p.lvl_cap = g->lvl_cap;
+  p.st = g->d_st;
+  p.bar_arrive = g->d_arrive;
+  p.spin_ns = g->spin_ns;
+  p.debug_flags = 0;
+  const bool timed = stats != nullptr;
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
+  CUDA_TRY(cudaMemsetAsync(L, 0xFF, sizeof(int32_t) * (size_t)k * n, g->stream));
+  if (Pp) CUDA_TRY(cudaMemsetAsync(Pp, 0xFF, sizeof(int32_t) * (size_t)k * n, g->stream));
+  CUDA_TRY(cudaMemsetAsync(g->d_arrive, 0, sizeof(int32_t) * ((size_t)(g->ms_ctas + 3) / 4 * 4), g->stream));
+  const int cgrid = std::max(1, std::min(g->sms * 8, (int)((n + kThreads - 1) / kThreads)));
+  k_msbfs_clear<<<cgrid, kThreads, 0, g->stream>>>(p);
+  CUDA_TRY(cudaGetLastError());
+  k_msbfs_sources<<<1, 64, 0, g->stream>>>(p, g->d_groups, g->d_masks, groups, g->d_groups + 64, g->d_groups + 128);
+  CUDA_TRY(cudaGetLastError());
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
+  void* args[] = {&p};
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_msbfs, dim3(g->ms_ctas), dim3(kThreads), args, 0, g->stream));
+  if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
+  if (stats) {
+    k_msbfs_counts<<<g->ms_ctas, kThreads, 0, g->stream>>>(p, g->d_counts);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (!lvl_dev)
+    CUDA_TRY(cudaMemcpyAsync(levels_out, L, sizeof(int32_t) * (size_t)k * n, cudaMemcpyDeviceToHost, g->stream));
+  if (parents_out && !par_dev)
+    CUDA_TRY(cudaMemcpyAsync(parents_out, Pp, sizeof(int32_t) * (size_t)k * n, cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaMemcpyAsync(g->h_st, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  if (g->h_st->err == BFS_E_TIMEOUT) return fail(BFS_E_TIMEOUT, "device wait %d ran out (batch)", g->h_st->err_where);
+  if (g->h_st->err != 0) return fail(g->h_st->err, "device error %d (batch)", g->h_st->err);
+  if (!stats) return BFS_OK;
+  float ms_loop = 0.f, ms_all = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms_loop, g->ev[1], g->ev[2]));
+  CUDA_TRY(cudaEventElapsedTime(&ms_all, g->ev[0], g->ev[2]));
+  const int L_used = std::min(g->h_st->num_levels, g->lvl_cap);
+  std::vector<unsigned long long> bits((size_t)std::max(L_used, 1));
+  if (L_used > 0)
+    CUDA_TRY(cudaMemcpy(bits.data(), g->d_level_bits, sizeof(unsigned long long) * (size_t)L_used,
+                        cudaMemcpyDeviceToHost));
+  std::vector<long long> counts((size_t)g->ms_ctas * 128), bedges((size_t)g->ms_ctas);
+  CUDA_TRY(cudaMemcpy(counts.data(), g->d_counts, sizeof(long long) * counts.size(), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(bedges.data(), g->d_block_edges, sizeof(long long) * bedges.size(), cudaMemcpyDeviceToHost));
+  long long work = 0;
+  for (long long x : bedges) work += x;
+  for (int i = 0; i < k; ++i) {
+    bfs_stats& st = stats[i];
+    long long reached = 0, edges = 0;
+    for (int b = 0; b < g->ms_ctas; ++b) {
+      reached += counts[(size_t)b * 128 + i];
+      edges += counts[(size_t)b * 128 + 64 + i];
+    }
+    int levels = 1;
+    for (int l = 0; l < L_used; ++l)
+      if ((bits[(size_t)l] >> i) & 1ull) levels = l + 2;
+    st.num_levels = levels;
+    st.active_ctas = g->ms_ctas;
+    st.reached = reached;
+    st.edges_scanned = edges;
+    st.candidates = reached - 1;
+    st.ms_level_step = ms_loop;
+    st.ms_total = ms_all;
+    st.work_edges = work;
+  }
+  return BFS_OK;
+}
+
 extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32_t* levels_out,
                              int32_t* parents_out, bfs_stats* stats) {
   if (!g) return fail(BFS_E_INVAL, "graph is NULL");
@@ -714,6 +900,17 @@ extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32
   CUDA_TRY(cudaGetDevice(&cur));
   if (cur != g->device) CUDA_TRY(cudaSetDevice(g->device));
   int rc = BFS_OK;
+  if (g->symmetric && g->batch_bitmask >= 0 && k >= 2) {
+    // groups of up to 64 sources share one bitmask traversal
+    rc = ms_setup(g);
+    for (int32_t i = 0; i < k && rc == BFS_OK; i += 64) {
+      const int kk = std::min(64, k - i);
+      rc = run_group_bitmask(g, srcs + i, kk, levels_out + (size_t)i * g->n,
+                             parents_out ? parents_out + (size_t)i * g->n : nullptr, stats ? stats + i : nullptr);
+    }
+    if (cur != g->device) cudaSetDevice(cur);
+    return rc;
+  }
   for (int32_t i = 0; i < k && rc == BFS_OK; ++i) {
     rc = run_one(g, srcs[i], levels_out + (size_t)i * g->n, parents_out ? parents_out + (size_t)i * g->n : nullptr,
                  stats ? stats + i : nullptr);

@@ -241,7 +241,8 @@ __device__ __forceinline__ int sm_id() {
   return s;
 }
 
-__device__ __forceinline__ void set_err(const Params& p, int code, int where) {
+template <class P>
+__device__ __forceinline__ void set_err(const P& p, int code, int where) {
   st_relaxed(&p.st->err_where, where);
   st_relaxed(&p.st->err, code);
 }
@@ -278,7 +279,8 @@ __host__ __device__ inline void level_sizing(int e_l, int P, int grain, int work
 // error word is set and all CTAs return false.  Also returns false, in every
 // CTA, when any CTA raised an error before the barrier.
 // ---------------------------------------------------------------------------
-__device__ bool grid_sync(const Params& p, int epoch) {
+template <class P>
+__device__ bool grid_sync(const P& p, int epoch) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -315,3 +315,74 @@ def test_barrier_wait_limit_reports_timeout():
         check_against_oracle(d, s)
     finally:
         d.close()
+
+
+# ---------------------------------------------------------------------------
+# multi-source batches with bitmask frontiers (BFS_SYMMETRIC graphs)
+# ---------------------------------------------------------------------------
+
+def _batch_check(rp, ci, srcs, flags, host=False, parents=True, **opts):
+    import torch
+    n = len(rp) - 1
+    k = len(srcs)
+    g = B.bfs_create_csr(n, len(ci), rp, ci, flags, make_opts(**opts) if opts else None,
+                         torch.cuda.current_stream().cuda_stream)
+    try:
+        S = np.ascontiguousarray(srcs, np.int32)
+        if host:
+            L = np.empty(k * n, np.int32)
+            P = np.empty(k * n, np.int32) if parents else None
+        else:
+            L = torch.empty(k * n, dtype=torch.int32, device="cuda")
+            P = torch.empty(k * n, dtype=torch.int32, device="cuda") if parents else None
+        st = (B.bfs_stats * k)()
+        B.bfs_run_batch(g, S, k, L, P, st)
+        L = (L if host else L.cpu().numpy()).reshape(k, n)
+        if parents:
+            P = (P if host else P.cpu().numpy()).reshape(k, n)
+        orc = oracle.Oracle(rp, ci)
+        keys = oracle.edge_keys(rp, ci)
+        for i, s in enumerate(S):
+            want, _ = orc.bfs(int(s))
+            assert np.array_equal(L[i], want), f"source {i} ({s}): levels differ"
+            if parents:
+                oracle.check_bfs_tree(rp, ci, int(s), L[i], P[i], keys=keys)
+            n_l, e_l = oracle.level_profile(rp, want)
+            assert st[i].reached == int(n_l.sum())
+            assert st[i].edges_scanned == int(e_l.sum())
+            assert st[i].num_levels == len(n_l)
+    finally:
+        B.bfs_destroy(g)
+
+
+@pytest.mark.parametrize("k", [2, 3, 64, 65, 130])
+def test_batch_bitmask_rmat16(rmat16, k):
+    rp, ci, srcs, _ = rmat16
+    S = np.resize(srcs, k)                      # k > 64 repeats sources: duplicates are allowed
+    _batch_check(rp, ci, S, B.BFS_VALIDATE | B.BFS_SYMMETRIC)
+
+
+@pytest.mark.parametrize("variant", ["host", "noparent", "relabel", "host_relabel"])
+def test_batch_bitmask_variants(rmat16, variant):
+    rp, ci, srcs, _ = rmat16
+    kw = {}
+    if "relabel" in variant:
+        kw["relabel"] = 1
+    _batch_check(rp, ci, srcs[:40], B.BFS_VALIDATE | B.BFS_SYMMETRIC, host="host" in variant,
+                 parents=variant != "noparent", **kw)
+
+
+def test_batch_bitmask_er_and_grid():
+    for rp, ci in (graphgen.erdos_renyi(1 << 15, 1 << 18, seed=4), graphgen.grid(64, 80, 0.02, seed=3)):
+        srcs = graphgen.sample_sources(rp, 64, seed=2)
+        _batch_check(rp, ci, srcs, B.BFS_VALIDATE | B.BFS_SYMMETRIC)
+
+
+def test_batch_bitmask_off_and_asymmetric_rejected():
+    rp, ci = graphgen.rmat(12, 16, seed=3)
+    srcs = graphgen.sample_sources(rp, 8, seed=2)
+    _batch_check(rp, ci, srcs, B.BFS_VALIDATE | B.BFS_SYMMETRIC, batch_bitmask=-1)
+    rp2, ci2 = _directed_csr(5, [(0, 1), (1, 2)])
+    with pytest.raises(B.BFSError) as e:
+        B.bfs_create_csr(5, len(ci2), rp2, ci2, B.BFS_VALIDATE | B.BFS_SYMMETRIC)
+    assert e.value.code == B.BFS_E_INVAL
