@@ -290,6 +290,9 @@ def main():
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--work-insensitive", action="store_true")
     ap.add_argument("--relabel", type=int, default=0, help="bfs_opts.relabel: 0 auto, 1 always, -1 off")
+    ap.add_argument("--small-level-edges", type=int, default=0,
+                    help="bfs_opts.small_level_edges: 0 default, -1 off")
+    ap.add_argument("--cta-warps", type=int, default=0, help="bfs_opts.cta_warps: 0 auto, 8 or 32")
     ap.add_argument("--per-phase", action="store_true", help="one launch per phase instead of the persistent loop")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dump", default="", help="write per-traversal records of the timed steps (JSON) here")
@@ -333,6 +336,8 @@ def main():
     opts.work_insensitive = 1 if args.work_insensitive else 0
     opts.persistent = -1 if args.per_phase else 0
     opts.relabel = args.relabel
+    opts.small_level_edges = args.small_level_edges
+    opts.cta_warps = args.cta_warps
     g = B.bfs_create_csr(n, nnz, rp, ci, B.BFS_VALIDATE, opts, stream.cuda_stream)
     info = B.bfs_graph_info(g)
     level = torch.empty(n, dtype=torch.int32, device=dev)

@@ -50,8 +50,8 @@ typedef struct bfs_opts {
                                P_l = min(P, ceil(e_l / chunk_edges)) warps, the
                                work-sensitive count of Fig. 1 lines 11/16 (the
                                paper's own formula is chunk_edges = 1).  Default 64 */
-  int32_t ctas;             /* persistent grid size G (CTAs of 1024 threads); 0 = every
-                               CTA that can be co-resident on the device */
+  int32_t ctas;             /* persistent grid size G in CTAs; 0 = every CTA that can be
+                               co-resident on the device */
   int32_t persistent;       /* 1 (default): one cooperative launch runs all levels,
                                separated by device grid barriers; -1: one launch per
                                phase with a host read of the level sizes in between */
@@ -69,6 +69,15 @@ typedef struct bfs_opts {
   int32_t batch_bitmask;    /* bfs_run_batch on a BFS_SYMMETRIC graph: 0 (default) =
                                groups of up to 64 sources share one traversal with a
                                64-bit mask per vertex; -1 = one traversal per source */
+  int32_t small_level_edges;/* a level with at most this many edges (and the small
+                               levels that follow it) runs on one CTA with CTA
+                               barriers while the rest of the grid waits at one grid
+                               barrier: high-diameter graphs have thousands of tiny
+                               levels.  0 = default (256 per warp of one CTA: 8192 with
+                               32-warp CTAs, 2048 with 8-warp CTAs), -1 = never */
+  int32_t cta_warps;        /* warps per CTA of the level loop: 32 (one CTA per SM,
+                               one copy of the shared-memory visited bits) or 8;
+                               0 = 32 when visited bits are kept, else 8 */
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */

@@ -44,6 +44,8 @@ class bfs_opts(ctypes.Structure):
         ("debug_flags", ctypes.c_int32),
         ("relabel", ctypes.c_int32),
         ("batch_bitmask", ctypes.c_int32),
+        ("small_level_edges", ctypes.c_int32),
+        ("cta_warps", ctypes.c_int32),
     ]
 
 

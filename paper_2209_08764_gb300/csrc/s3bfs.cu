@@ -30,6 +30,13 @@ int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vec
 // dynamic shared memory of the level loop: the visited bits
 static size_t loop_smem(int hub_n) { return (size_t)hub_n / 8; }
 
+template <int W>
+__global__ void k_level_loop(Params p);
+// the level loop for a CTA shape
+static const void* level_loop_fn(int wpc) {
+  return wpc == 32 ? (const void*)k_level_loop<32> : (const void*)k_level_loop<8>;
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -89,77 +96,141 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
     st->num_levels = 0;
     st->bar_release = 0;
     st->reached = st->edges = st->cands = 0;
+    st->progress = 0;
+    st->resume_level = 0;
   }
 }
 
-// The whole level loop in one cooperative launch: explore, grid barrier,
-// compact, grid barrier, per level.  Warps beyond P_l skip the level's work
-// and wait at the barrier (parked), so a small level occupies few SMs.
-__global__ void __launch_bounds__(kThreads, S3BFS_MIN_CTAS) k_level_loop(Params p) {
-  extern __shared__ __align__(16) uint32_t s_hub[];  // visited bits, p.hub_n / 8 bytes
+// The whole level loop runs in one cooperative launch (k_level_loop).  A
+// level with at most p.small_edges edges starts a streak that CTA 0 runs
+// alone while the levels stay that small (the others wait at one grid
+// barrier); every other level runs on the whole grid.  Warps beyond P_l skip
+// the level's work and wait at the barrier, so a small level occupies few SMs.
+//
+// One level of the loop (explore, barrier, compact, barrier).  GRID: all
+// CTAs with grid barriers.  Otherwise CTA 0 alone, its warps taking the
+// chunks, with CTA barriers (small levels).  Returns false if the traversal
+// must stop (an error, including a wait that ran out).
+template <int W>
+__device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e_l, int* bar, uint32_t* s_hub,
+                                       long long* acc, bool GRID) {
+  __shared__ int s_err;
   const int lane = threadIdx.x & (kWarp - 1);
-  const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
-  const int P = gridDim.x * kWarpsPerCta;
+  const int gw = GRID ? blockIdx.x * W + (threadIdx.x >> 5) : (threadIdx.x >> 5);
+  const int P = GRID ? gridDim.x * W : W;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const int par = l & 1;
+  int P_l, C_l;
+  level_sizing(e_l, P, p.grain, p.work_insensitive, &P_l, &C_l);
+  long long t_level = 0;
+  if (leader) {
+    t_level = global_ns();
+    acc[0] += n_l;
+    acc[1] += e_l;
+    record_level(p, l, n_l, e_l, P_l);
+  }
+  // big level: take the visited-bits snapshot into shared memory
+  const int hub_lim = (GRID && p.hub_n > 0 && e_l >= p.hub_n) ? load_hub_bits(p, s_hub) : 0;
+  int cnt = 0, e_begin = 0;
+  if (gw < P_l) {
+    const long long eb = (long long)gw * C_l;
+    e_begin = (int)min(eb, (long long)e_l);
+    const int e_end = (int)min(eb + C_l, (long long)e_l);
+    if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
+  }
+  if (GRID) {
+    if (!grid_sync(p, ++*bar)) return false;
+  } else {
+    __syncthreads();
+  }
+  if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
+  if (GRID && p.hub_n > 0) build_hub_bits(p, gw, P);
+  if (P_l == 0) {
+    if (gw == 0 && lane == 0) publish_empty_next(p, par);
+  } else if (!GRID || (int)blockIdx.x * W < P_l) {
+    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
+  }
+  if (GRID) {
+    if (!grid_sync(p, ++*bar)) return false;
+  } else {
+    __syncthreads();
+    if (threadIdx.x == 0) s_err = ld_relaxed(&p.st->err);
+    __syncthreads();
+    if (s_err != 0) return false;
+  }
+  if (leader) {
+    acc[2] += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+    if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
+  }
+  return true;
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_level_loop(Params p) {
+  extern __shared__ __align__(16) uint32_t s_hub[];  // visited bits, p.hub_n / 8 bytes
+  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
+  const int P = gridDim.x * W;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) p.cta_smid[blockIdx.x] = sm_id();
   int bar = 0, l = 0;
-  long long reached = 0, edges = 0, cands = 0;
+  long long acc[3] = {0, 0, 0};  // reached, edges, candidates (leader)
+  bool streak = false;           // CTA 0 is running small levels alone
   while (true) {
-    const int par = l & 1;
-    const int n_l = ld_relaxed(&p.st->ctrl[par].n);
-    const int e_l = ld_relaxed(&p.st->ctrl[par].e);
+    const int n_l = ld_relaxed(&p.st->ctrl[l & 1].n);
+    const int e_l = ld_relaxed(&p.st->ctrl[l & 1].e);
+    const bool small = n_l > 0 && p.small_edges > 0 && e_l <= p.small_edges;
+    if (streak && !small) {
+      // CTA 0 ends its streak: the whole grid resumes at level l (or stops)
+      streak = false;
+      if (threadIdx.x == 0) st_relaxed(&p.st->resume_level, l);
+      if (!grid_sync(p, ++bar)) break;
+      if (p.hub_n > 0) {
+        // the visited bits were not kept up to date by the streak
+        build_hub_bits(p, gw, P);
+        if (!grid_sync(p, ++bar)) break;
+      }
+      continue;
+    }
     if (n_l <= 0) break;
     if (l + 2 >= (int)kEpochMask) {
       if (leader) set_err(p, BFS_E_INVAL, 5);
       break;
     }
-    int P_l, C_l;
-    level_sizing(e_l, P, p.grain, p.work_insensitive, &P_l, &C_l);
-    long long t_level = 0;
-    if (leader) {
-      t_level = global_ns();
-      reached += n_l;
-      edges += e_l;
-      record_level(p, l, n_l, e_l, P_l);
+    if (small && blockIdx.x != 0) {
+      // parked at one grid barrier while CTA 0 runs the small levels
+      if (!grid_sync(p, ++bar)) break;
+      l = ld_relaxed(&p.st->resume_level);
+      if (p.hub_n > 0) {
+        build_hub_bits(p, gw, P);
+        if (!grid_sync(p, ++bar)) break;
+      }
+      continue;
     }
-    // big level: take the visited-bits snapshot into shared memory
-    const int hub_lim = (p.hub_n > 0 && e_l >= p.hub_n) ? load_hub_bits(p, s_hub) : 0;
-    int cnt = 0, e_begin = 0;
-    if (gw < P_l) {
-      const long long eb = (long long)gw * C_l;
-      e_begin = (int)min(eb, (long long)e_l);
-      const int e_end = (int)min(eb + C_l, (long long)e_l);
-      if (e_begin < e_end)
-        cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
-    }
-    if (!grid_sync(p, ++bar)) break;
-    if (leader && l < p.lvl_cap)
-      p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
-    if (p.hub_n > 0) build_hub_bits(p, gw, P);
-    if (P_l == 0) {
-      if (gw == 0 && lane == 0) publish_empty_next(p, par);
-    } else if ((int)blockIdx.x * kWarpsPerCta < P_l) {
-      compact_cta(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
-    }
-    if (!grid_sync(p, ++bar)) break;
-    if (leader) {
-      cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
-      if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
+    streak = small;
+    if (!one_level<W>(p, l, n_l, e_l, &bar, s_hub, acc, !small)) {
+      if (streak) {
+        // release the parked CTAs; the error word makes everybody stop
+        if (threadIdx.x == 0) st_relaxed(&p.st->resume_level, l);
+        grid_sync(p, ++bar);
+      }
+      break;
     }
     ++l;
+    if (small && threadIdx.x == 0) st_relaxed(&p.st->progress, l);
   }
   if (leader) {
     p.st->num_levels = l;
-    p.st->reached = reached;
-    p.st->edges = edges;
-    p.st->cands = cands;
+    p.st->reached = acc[0];
+    p.st->edges = acc[1];
+    p.st->cands = acc[2];
   }
 }
 
 // Launch-per-phase mode: the same two phases as separate launches; the host
 // reads n and e of the next level in between.
-__global__ void __launch_bounds__(kThreads) k_explore(Params p, int l, int n_l, int e_l, int P_l, int C_l) {
-  const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+template <int W>
+__global__ void __launch_bounds__(W * kWarp) k_explore(Params p, int l, int n_l, int e_l, int P_l, int C_l) {
+  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
   if (blockIdx.x == 0 && threadIdx.x == 0) record_level(p, l, n_l, e_l, P_l);
   if (gw >= P_l) return;
   const long long eb = (long long)gw * C_l;
@@ -170,8 +241,9 @@ __global__ void __launch_bounds__(kThreads) k_explore(Params p, int l, int n_l, 
   if ((threadIdx.x & (kWarp - 1)) == 0) p.cand_cnt[gw] = cnt;
 }
 
-__global__ void __launch_bounds__(kThreads) k_compact(Params p, int l, int e_l, int P_l, int C_l) {
-  const int gw = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+template <int W>
+__global__ void __launch_bounds__(W * kWarp) k_compact(Params p, int l, int e_l, int P_l, int C_l) {
+  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
   const int par = l & 1;
   if (P_l == 0) {
     if (gw == 0 && (threadIdx.x & (kWarp - 1)) == 0) publish_empty_next(p, par);
@@ -180,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(Params p, int l, int e_l, 
   // every thread of the CTA takes part; warps without a chunk bring 0
   const int e_begin = gw < P_l ? (int)min((long long)gw * C_l, (long long)e_l) : 0;
   const int cnt = gw < P_l ? ld_relaxed(&p.cand_cnt[gw]) : 0;
-  compact_cta(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
+  compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
 }
 
 // CSR sanity checks that every traversal relies on (no out-of-range access):
@@ -222,11 +294,13 @@ struct bfs_graph {
   int sms = 0;
   int ctas = 0;   // G
   int warps = 0;  // P
+  int wpc = 32;   // warps per CTA of the level loop (8 or 32)
   int grain = 64;
   int persistent = 1;
   int work_insensitive = 0;
   int debug_flags = 0;
   long long spin_ns = 1000000000ll;
+  int small_edges = -1;  // resolved at create: 256 edges per warp of one CTA
   int32_t lvl_cap = 0;
   int hub_n = 0;         // vertices [0, hub_n) have visited bits in shared memory
   bool relabel = false;  // internal ids are degree-descending (hubs first)
@@ -358,6 +432,8 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     if (opts->spin_limit_ms > 0) g->spin_ns = (long long)opts->spin_limit_ms * 1000000ll;
     g->debug_flags = opts->debug_flags;
     g->batch_bitmask = opts->batch_bitmask;
+    if (opts->small_level_edges > 0) g->small_edges = opts->small_level_edges;
+    if (opts->small_level_edges < 0) g->small_edges = 0;  // never
   }
   g->symmetric = (flags & BFS_SYMMETRIC) != 0;
   if (!coop) g->persistent = 0;
@@ -459,14 +535,21 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   CUDA_TRY(cudaMemsetAsync(g->d_col_idx, 0, sizeof(int32_t) * nnz_pad, g->stream));
   if (nnz) CUDA_TRY(cudaMemcpyAsync(g->d_col_idx, ci, sizeof(int32_t) * (size_t)nnz, kind, g->stream));
 
+  // CTA shape: one CTA of 32 warps per SM when the visited bits are in shared
+  // memory (one copy per SM), else 8-warp CTAs (more SMs share a small level)
+  const int cw = opts ? opts->cta_warps : 0;
+  if (cw != 0 && cw != 8 && cw != 32) return fail(BFS_E_INVAL, "cta_warps = %d: use 0, 8 or 32", cw);
+  g->wpc = cw ? cw : (g->hub_n > 0 ? 32 : 8);
   // persistent grid: every CTA that fits next to the shared-memory bits
-  CUDA_TRY(cudaFuncSetAttribute(k_level_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(g->hub_n)));
+  const void* loop_fn = level_loop_fn(g->wpc);
+  CUDA_TRY(cudaFuncSetAttribute(loop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(g->hub_n)));
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, loop_smem(g->hub_n)));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_fn, g->wpc * kWarp, loop_smem(g->hub_n)));
   if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
   g->ctas = per_sm * g->sms;
   if (opts && opts->ctas > 0) g->ctas = std::min(g->ctas, (int)opts->ctas);
-  g->warps = g->ctas * kWarpsPerCta;
+  g->warps = g->ctas * g->wpc;
+  if (g->small_edges < 0) g->small_edges = 256 * g->wpc;
 
   // work memory
   if (g->hub_n > 0 && (rc = dalloc(g, &g->d_hub_bits, (size_t)g->hub_n / 32)) != BFS_OK) return rc;
@@ -571,6 +654,7 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.spin_ns = g->spin_ns;
   p.hub_bits = g->d_hub_bits;
   p.hub_n = g->persistent ? g->hub_n : 0;
+  p.small_edges = g->persistent ? g->small_edges : 0;
   return p;
 }
 
@@ -584,7 +668,7 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
   if (g->persistent) {
     Params pc = p;
     void* args[] = {&pc};
-    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(g->ctas), dim3(kThreads), args,
+    CUDA_TRY(cudaLaunchCooperativeKernel(level_loop_fn(g->wpc), dim3(g->ctas), dim3(g->wpc * kWarp), args,
                                          loop_smem(p.hub_n), g->stream));
   } else {
     // launch per phase; the host reads n and e of every level
@@ -599,10 +683,16 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
       level_sizing(e_l, g->warps, g->grain, g->work_insensitive, &P_l, &C_l);
       reached += n_l;
       edges += e_l;
-      const int grid = std::max(1, (P_l + kWarpsPerCta - 1) / kWarpsPerCta);
-      k_explore<<<grid, kThreads, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
-      CUDA_TRY(cudaGetLastError());
-      k_compact<<<grid, kThreads, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+      const int grid = std::max(1, (P_l + g->wpc - 1) / g->wpc);
+      if (g->wpc == 32) {
+        k_explore<32><<<grid, 32 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+        CUDA_TRY(cudaGetLastError());
+        k_compact<32><<<grid, 32 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+      } else {
+        k_explore<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+        CUDA_TRY(cudaGetLastError());
+        k_compact<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+      }
       CUDA_TRY(cudaGetLastError());
       CUDA_TRY(cudaMemcpyAsync(hc, &g->d_st->ctrl[(l + 1) & 1], sizeof(LevelCtrl), cudaMemcpyDeviceToHost,
                                g->stream));
@@ -677,7 +767,7 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
     }
     for (int l = 0; l < L; ++l) {
       int32_t* r = stats->per_level + (size_t)l * kLevelFields;
-      const int ctas = std::min(g->ctas, (r[3] + kWarpsPerCta - 1) / kWarpsPerCta);
+      const int ctas = std::min(g->ctas, (r[3] + g->wpc - 1) / g->wpc);
       r[4] = g->persistent ? distinct[ctas] : -1;
       if (!g->persistent) r[5] = r[6] = -1;
     }
@@ -948,7 +1038,7 @@ constexpr size_t kNaBad = na_align(sizeof(DevState));
 constexpr size_t kNaArrive = kNaBad + 256;
 constexpr size_t kNaSmid = kNaArrive + na_align(sizeof(int32_t) * kNoAllocMaxCtas);
 constexpr size_t kNaStatus = kNaSmid + na_align(sizeof(int32_t) * kNoAllocMaxCtas);
-constexpr size_t kNaFront = kNaStatus + na_align(sizeof(ChunkStatus) * kNoAllocMaxCtas * kWarpsPerCta);
+constexpr size_t kNaFront = kNaStatus + na_align(sizeof(ChunkStatus) * kNoAllocMaxCtas * 32);
 constexpr size_t kNaFrontOne = na_align(sizeof(int32_t) * (kNoAllocMaxN + 4));
 constexpr size_t kNaCol = kNaFront + 6 * kNaFrontOne;
 constexpr size_t kNaCand = kNaCol + na_align(sizeof(int32_t) * (kNoAllocMaxNnz + 8));
@@ -983,7 +1073,7 @@ static int noalloc_setup(int dev, NoAllocDevice** out) {
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return fail(BFS_E_CUDA, "device %d has no cooperative launch", dev);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop, kThreads, loop_smem(0)));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop<32>, 32 * kWarp, loop_smem(0)));
     if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
     d.scratch = static_cast<unsigned char*>(ptr);
     d.sms = sms;
@@ -1054,18 +1144,19 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   p.grain = 64;
   p.work_insensitive = 0;
   p.src = src;
-  p.max_chunks = d->ctas * kWarpsPerCta;
+  p.max_chunks = d->ctas * 32;
   p.debug_flags = 0;
   p.spin_ns = 1000000000ll;
   p.hub_bits = nullptr;
   p.hub_n = 0;
+  p.small_edges = 256 * 32;
 
   // k_init clears the look-back and barrier state left by the previous call
   const int igrid = std::max(1, std::min(d->sms * 8, (int)(((long long)n / 4 + 255) / 256)));
   k_init<<<igrid, kThreads, 0, stream>>>(p, d->ctas);
   CUDA_TRY(cudaGetLastError());
   void* args[] = {&p};
-  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop, dim3(d->ctas), dim3(kThreads), args, loop_smem(0),
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop<32>, dim3(d->ctas), dim3(32 * kWarp), args, loop_smem(0),
                                        stream));
   DevState h;
   CUDA_TRY(cudaMemcpyAsync(&h, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));

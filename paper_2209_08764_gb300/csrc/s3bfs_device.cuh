@@ -99,6 +99,8 @@ struct DevState {
   int32_t num_levels;
   int32_t bar_release;
   long long reached, edges, cands;
+  int32_t progress;      // levels done by CTA 0 alone (the others wait; progress extends their wait)
+  int32_t resume_level;  // level at which the whole grid resumes after CTA 0 ran small levels alone
 };
 
 struct Params {
@@ -130,6 +132,9 @@ struct Params {
   // at the start of a level with at least hub_n edges
   uint32_t* hub_bits;
   int32_t hub_n;
+  // levels with at most this many edges run on CTA 0 alone, with CTA barriers
+  // instead of grid barriers (0 = never)
+  int32_t small_edges;
 };
 
 // ---------------------------------------------------------------------------
@@ -324,11 +329,21 @@ __device__ bool grid_sync(const P& p, int epoch) {
   }
   if (threadIdx.x == 0) {
     int ok = 1, it = 0;
-    const long long t0 = global_ns();
+    long long t0 = global_ns();
+    int prog = ld_relaxed(&p.st->progress);
     while (ld_acquire(&p.st->bar_release) < epoch) {
       if (ld_relaxed(&p.st->err) != 0) {
         ok = 0;
         break;
+      }
+      if ((it & 127) == 127) {
+        // CTA 0 working alone through small levels is progress, not a stall
+        const int pr = ld_relaxed(&p.st->progress);
+        if (pr != prog) {
+          prog = pr;
+          t0 = global_ns();
+          it = 0;
+        }
       }
       if (++it > kSpinIters || global_ns() - t0 > p.spin_ns) {
         set_err(p, BFS_E_TIMEOUT, 2);
@@ -519,9 +534,10 @@ __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, 
 // next level's n and e.  Returns false (in every thread) if a wait ran out.
 constexpr int kCompactR = S3BFS_CR;
 
+template <int W>  // warps per CTA
 __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt) {
-  __shared__ int sK[kWarpsPerCta], sD[kWarpsPerCta], sC[kWarpsPerCta];
-  __shared__ int sRed[3][kWarpsPerCta];
+  __shared__ int sK[W], sD[W], sC[W];
+  __shared__ int sRed[3][W];
   __shared__ int sPre[3];
   const int lane = threadIdx.x & (kWarp - 1);
   const int wib = threadIdx.x >> 5;
@@ -589,7 +605,7 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
   if (threadIdx.x == 0) {
     int Kc = 0, Dc = 0, Cc = 0;
 #pragma unroll
-    for (int w = 0; w < kWarpsPerCta; ++w) {
+    for (int w = 0; w < W; ++w) {
       Kc += sK[w];
       Dc += sD[w];
       Cc += sC[w];
@@ -637,7 +653,7 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
   if (threadIdx.x == 0) {
     int a = 0, d = 0, c = 0;
 #pragma unroll
-    for (int w = 0; w < kWarpsPerCta; ++w) {
+    for (int w = 0; w < W; ++w) {
       a += sRed[0][w];
       d += sRed[1][w];
       c += sRed[2][w];
@@ -685,10 +701,10 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
       EXn[pos] = Dx + dpre[r];
     }
   }
-  if (b == (P_l - 1) / kWarpsPerCta && threadIdx.x == 0) {
+  if (b == (P_l - 1) / W && threadIdx.x == 0) {
     long long n_next = sPre[0], e_next = sPre[1], c_l = sPre[2];
 #pragma unroll
-    for (int w = 0; w < kWarpsPerCta; ++w) {
+    for (int w = 0; w < W; ++w) {
       n_next += sK[w];
       e_next += sD[w];
       c_l += sC[w];

@@ -19,6 +19,9 @@ class Dev:
 
     def __init__(self, rp, ci, flags=B.BFS_VALIDATE, **opts):
         import torch
+        sl = opts.get("small_level_edges", 0)
+        self._small_opt = sl
+        self.persistent = opts.get("persistent", 0) >= 0
         self.torch = torch
         self.rp = np.ascontiguousarray(rp, np.int32)
         self.ci = np.ascontiguousarray(ci, np.int32)
@@ -26,6 +29,9 @@ class Dev:
         self.g = B.bfs_create_csr(self.n, len(self.ci), self.rp, self.ci if len(self.ci) else None, flags,
                                   make_opts(**opts) if opts else None, torch.cuda.current_stream().cuda_stream)
         self.info = B.bfs_graph_info(self.g)
+        # levels with at most this many edges run on one CTA (small-level mode)
+        wpc = self.info["warps"] // self.info["ctas"]
+        self.small = 256 * wpc if self._small_opt == 0 else (0 if self._small_opt < 0 else self._small_opt)
         self.level = torch.empty(self.n, dtype=torch.int32, device="cuda")
         self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
 
@@ -76,7 +82,9 @@ def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=64
         assert np.all(pl[:L, 2] >= nxt) and np.all(pl[:L, 2] <= e_next), "candidates out of bounds"
         assert st.candidates == int(pl[:, 2].sum()) or L < len(n_l)
         P = dev.info["warps"]
-        want_P = np.where(e_l[:L] > 0, np.minimum(P, -(-e_l[:L] // grain)), 0)
+        W = P // dev.info["ctas"]
+        small = (e_l[:L] <= dev.small) & dev.persistent
+        want_P = np.where(e_l[:L] > 0, np.minimum(np.where(small, W, P), -(-e_l[:L] // grain)), 0)
         if "wi" not in dev.__dict__:
             assert np.array_equal(pl[:L, 3], want_P), "active warps != min(P, ceil(e_l/grain))"
     return lv, par, st, pl

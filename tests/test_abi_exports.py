@@ -51,8 +51,8 @@ def test_host_only_calls(lib):
 
 
 def test_struct_layout_matches_header():
-    # int32 x 8
-    assert ctypes.sizeof(B.bfs_opts) == 32
+    # int32 x 10
+    assert ctypes.sizeof(B.bfs_opts) == 40
     # 2 int32, 3 int64, 2 float, pointer, int32 (+ padding), int64
     assert B.bfs_stats.per_level.offset == 40
     assert B.bfs_stats.work_edges.offset == 56

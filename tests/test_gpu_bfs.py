@@ -104,6 +104,10 @@ def test_rmat16_64_sources(rmat16):
     dict(persistent=-1), dict(persistent=-1, chunk_edges=5), dict(work_insensitive=1),
     dict(work_insensitive=1, ctas=2), dict(relabel=1), dict(relabel=-1), dict(relabel=1, chunk_edges=1, ctas=7),
     dict(relabel=1, persistent=-1), dict(relabel=1, work_insensitive=1),
+    dict(small_level_edges=-1), dict(small_level_edges=1 << 22), dict(small_level_edges=3000),
+    dict(small_level_edges=1 << 22, relabel=1), dict(small_level_edges=-1, relabel=-1),
+    dict(cta_warps=8), dict(cta_warps=8, ctas=3), dict(cta_warps=8, small_level_edges=-1),
+    dict(cta_warps=8, persistent=-1), dict(cta_warps=32, relabel=-1), dict(cta_warps=8, relabel=1),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_rmat16_launch_configurations(rmat16, opts):
     rp, ci, srcs, keys = rmat16
@@ -124,7 +128,9 @@ def test_work_insensitive_uses_every_warp(rmat16):
     try:
         _, _, st, pl = d.run(int(srcs[0]), per_level_cap=64)
         P = d.info["warps"]
-        assert np.all(pl[pl[:, 1] > 0, 3] == P)
+        big = pl[:, 1] > d.small
+        assert np.all(pl[big, 3] == P)
+        assert np.all(pl[(pl[:, 1] > 0) & ~big, 3] == P // d.info["ctas"])
     finally:
         d.close()
 
@@ -212,6 +218,29 @@ def test_run_batch_matches_single_runs(rmat16, relabel):
             want, _ = orc.bfs(int(S[i]))
             assert np.array_equal(Lh[i], want)
             assert st[i].reached == int((want >= 0).sum())
+    finally:
+        d.close()
+
+
+@pytest.mark.parametrize("small", [-1, 0, 1 << 20])
+@pytest.mark.parametrize("cw", [8, 32])
+def test_long_path_and_grid_small_level_mode(small, cw):
+    """Thousands of tiny levels: CTA 0 alone runs them (small-level mode), or
+    the whole grid with two grid barriers per level (small = -1)."""
+    n = 20000
+    rp, ci = graphgen.from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    d = Dev(rp, ci, small_level_edges=small, cta_warps=cw)
+    try:
+        lv, _, st, _ = check_against_oracle(d, 0)
+        assert st.num_levels == n
+        check_against_oracle(d, n // 3)
+    finally:
+        d.close()
+    rp, ci = graphgen.grid(300, 200, 0.05, seed=7)
+    d = Dev(rp, ci, small_level_edges=small, cta_warps=cw)
+    try:
+        check_against_oracle(d, 0)
+        check_against_oracle(d, 30000)
     finally:
         d.close()
 
