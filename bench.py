@@ -275,6 +275,114 @@ def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev):
         dist.destroy_process_group()
 
 
+def serving_pool():
+    """The 32-graph serving pool: R-MAT s12..s22 (11), ER mean degree 8 with
+    n = 2^12..2^22 (11), 4-neighbour grids 256^2..2048^2 with 1% of edges
+    deleted (7), R-MAT s14/s16/s18 with a second seed (3)."""
+    pool = []
+    for sc in range(12, 23):
+        pool.append((f"rmat{sc}", lambda sc=sc: graphgen.rmat(sc, 16, seed=1)))
+    for lg in range(12, 23):
+        pool.append((f"er{lg}", lambda lg=lg: graphgen.erdos_renyi(1 << lg, 4 << lg, seed=4)))
+    for side in (256, 362, 512, 724, 1024, 1448, 2048):
+        pool.append((f"grid{side}", lambda side=side: graphgen.grid(side, side, 0.01, seed=3)))
+    for sc in (14, 16, 18):
+        pool.append((f"rmat{sc}b", lambda sc=sc: graphgen.rmat(sc, 16, seed=2)))
+    return pool
+
+
+def run_serve_mode(args, B, torch):
+    """Continuous-batching server over the pool vs the same stream served one
+    query at a time by bfs_run (first come, first served)."""
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
+    pool = serving_pool()
+    graphs, handles, degs, nonisolated = [], [], [], []
+    for name, make in pool:
+        rp, ci = make()
+        h = B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, 0, None, stream.cuda_stream)
+        graphs.append((name, len(rp) - 1, len(ci)))
+        handles.append(h)
+        d = np.diff(rp.astype(np.int64))
+        degs.append(d)
+        nonisolated.append(np.nonzero(d > 0)[0].astype(np.int32))
+    t_gen = time.perf_counter() - t_gen
+    rng = np.random.default_rng(5)
+    N = args.serve_queries
+    gsel = rng.integers(0, len(pool), size=N)
+    srcs = np.array([nonisolated[g][rng.integers(len(nonisolated[g]))] for g in gsel], np.int32)
+    # service time of every query alone (plain single-source S3BFS through bfs_run)
+    maxn = max(n for _, n, _ in graphs)
+    lv = torch.empty(maxn, dtype=torch.int32, device="cuda")
+    for g in range(len(pool)):
+        B.bfs_run(handles[g], int(nonisolated[g][0]), lv, None, None)
+    torch.cuda.synchronize()
+    service = np.empty(N)
+    teps = np.empty(N, np.int64)
+    st = B.bfs_stats()
+    for i in range(N):
+        t0 = time.perf_counter()
+        B.bfs_run(handles[gsel[i]], int(srcs[i]), lv, None, st)
+        service[i] = time.perf_counter() - t0
+        teps[i] = st.edges_scanned // 2
+    capacity = 1.0 / service.mean()                       # queries per second, one at a time
+    lam = args.serve_load * capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=N))
+    # FCFS one at a time, from the measured service times
+    done_fcfs = np.empty(N)
+    t = 0.0
+    for i in range(N):
+        t = max(t, arrivals[i]) + service[i]
+        done_fcfs[i] = t
+    lat_fcfs = done_fcfs - arrivals
+    # the server, in real time
+    so = B.bfs_server_opts()
+    so.slots = args.serve_slots
+    srv = B.bfs_server_create(handles, so, stream.cuda_stream)
+    done = {}
+    nxt = 0
+    t0 = time.perf_counter()
+    while len(done) < N:
+        now = time.perf_counter() - t0
+        while nxt < N and arrivals[nxt] <= now:
+            B.bfs_server_submit(srv, int(gsel[nxt]), int(srcs[nxt]), None, None, nxt)
+            nxt += 1
+        q, r = B.bfs_server_pending(srv)
+        if q == 0 and r == 0:
+            if nxt < N:
+                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
+            continue
+        for c in B.bfs_server_poll(srv, 256):
+            done[c.tag] = c
+    makespan = time.perf_counter() - t0
+    B.bfs_server_destroy(srv)
+    # the library stamps completions with the host's monotonic clock, the
+    # clock time.perf_counter() reads on Linux: latency = done - arrival
+    lat = np.array([done[i].t_done_us * 1e-6 - (t0 + arrivals[i]) for i in range(N)])
+    clock_skew = float(np.median([done[i].t_submit_us * 1e-6 - (t0 + arrivals[i]) for i in range(N)]))
+    status_bad = sum(int(c.status != 0) for c in done.values())
+    gteps = float(teps.sum()) / makespan / 1e9
+    fcfs_makespan = done_fcfs[-1] - 0.0
+    line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "serving-pool32", "graphs": [g[0] for g in graphs], "queries": N,
+                       "load": args.serve_load, "lambda_qps": lam, "slots": args.serve_slots,
+                       "arrivals": "Poisson, graph uniform over the pool, source uniform over non-isolated, seed 5"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "mean": float(lat.mean() * 1e3)},
+            "fcfs_one_at_a_time": {"gteps": float(teps.sum()) / fcfs_makespan / 1e9,
+                                   "p50_ms": float(np.percentile(lat_fcfs, 50) * 1e3),
+                                   "p99_ms": float(np.percentile(lat_fcfs, 99) * 1e3),
+                                   "capacity_qps": capacity},
+            "failed": int(status_bad), "pool_build_s": round(t_gen, 1),
+            "median_submit_delay_ms": clock_skew * 1e3}
+    print(json.dumps(line), flush=True)
+    for h in handles:
+        B.bfs_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +408,12 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="all sources of a step in one bfs_run_batch call (64-source bitmask traversal)")
     ap.add_argument("--no-parents", action="store_true", help="levels only (batch mode)")
+    ap.add_argument("--serve", action="store_true",
+                    help="query server over the 32-graph pool: Poisson stream, p50/p99 latency")
+    ap.add_argument("--serve-queries", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="arrival rate as a fraction of the one-at-a-time capacity")
+    ap.add_argument("--serve-slots", type=int, default=64)
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.sources:
@@ -311,6 +425,9 @@ def main():
     import torch
     from paper_2209_08764_gb300 import binding as B
 
+    if args.serve:
+        run_serve_mode(args, B, torch)
+        return
     ws, rank, local = dist_setup()
     dist = None
     if ws > 1:

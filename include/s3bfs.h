@@ -230,6 +230,77 @@ int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, 
 int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col_idx, int32_t src,
                         int32_t *level_out, int32_t *parent_out, void *cuda_stream);
 
+/* ---- query server: continuous batching over a pool of graphs ------------ */
+
+typedef struct bfs_server bfs_server; /* opaque; owned by the library */
+
+typedef struct bfs_server_opts {
+  int32_t slots;             /* queries running at once (<= 128 and <= the grid's CTAs);
+                                0 = 64 */
+  int32_t levels_per_launch; /* levels each launch may run before the scheduler admits
+                                new queries; 0 = 8 (a launch also ends when a query
+                                finishes) */
+  int32_t chunk_edges;       /* grain, as bfs_opts.chunk_edges; 0 = 64 */
+  int32_t cta_warps;         /* 8 or 32 warps per CTA; 0 = 8 */
+  int32_t spin_limit_ms;     /* device wait limit; 0 = 1000 */
+  int32_t pad;
+  int64_t arena_bytes;       /* device memory for the working buffers of running
+                                queries (admission waits while it is full);
+                                0 = half of the free memory, at most 32 GiB */
+} bfs_server_opts;
+
+typedef struct bfs_completion {
+  int64_t tag;           /* the caller's tag from bfs_server_submit */
+  int32_t graph, src;
+  int32_t status;        /* BFS_OK or an error code (outputs undefined then) */
+  int32_t num_levels;
+  int64_t reached, edges_scanned;
+  double t_submit_us;    /* host steady clock, microseconds: submitted, */
+  double t_admit_us;     /* admitted (its memory taken, level 0 set), */
+  double t_done_us;      /* and seen finished, with its outputs written */
+} bfs_completion;
+
+/*
+ * bfs_server_create -- a server over ngraphs graphs made by bfs_create_csr on
+ * the current device (the graphs stay owned by the caller and must outlive
+ * the server).  Queries on any of them are admitted into free slots while
+ * their working memory (about 24 bytes per vertex and 12 per edge of their
+ * graph) fits in the server's arena, and run together: every level of every
+ * running query is the S3BFS level step of bfs_run (Fig. 1) on its share of
+ * the grid (at least one CTA, the rest in proportion to the level's edge
+ * count).  Batching queries is not in the paper.  cuda_stream as for
+ * bfs_create_csr.
+ */
+int bfs_server_create(bfs_graph *const *graphs, int32_t ngraphs, const bfs_server_opts *opts, void *cuda_stream,
+                      bfs_server **out);
+
+/*
+ * bfs_server_submit -- queue one traversal of graph `graph` (index into the
+ * create-time array) from src.  level_out / parent_out (nullable; both may be
+ * NULL to discard the result) receive the result as in bfs_run, device or
+ * host pointers; they must stay valid until the query's completion is
+ * returned by bfs_server_poll.  Host-side only: nothing runs until the next
+ * poll.  Errors: BFS_E_INVAL.
+ */
+int bfs_server_submit(bfs_server *s, int32_t graph, int32_t src, int32_t *level_out, int32_t *parent_out,
+                      int64_t tag);
+
+/*
+ * bfs_server_poll -- one scheduling round: admit queued queries, run one
+ * launch over every running query (it returns when a query finishes or after
+ * levels_per_launch levels), retire the finished ones.  Up to cap completion
+ * records are written to out (the rest are kept for later polls); *ndone is
+ * their number.  Blocks for the launch.  Call it in a loop while queries are
+ * queued or running (bfs_server_pending).
+ */
+int bfs_server_poll(bfs_server *s, bfs_completion *out, int32_t cap, int32_t *ndone);
+
+/* bfs_server_pending -- queries queued (not admitted) and running. */
+int bfs_server_pending(bfs_server *s, int32_t *queued, int32_t *running);
+
+/* bfs_server_destroy -- free the server (not the graphs).  NULL is a no-op. */
+void bfs_server_destroy(bfs_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,8 +1,9 @@
 """Build of the CUDA library ``libs3bfs.so`` (sm_103a) next to its sources.
 
-nvcc compiles the kernels + C ABI (``csrc/s3bfs.cu``) and g++ the host CSR
-helpers (``csrc/csr_host.cpp``) in parallel, then nvcc links a shared library
-with the CUDA runtime linked statically.  Objects go to ``_build/`` (ignored).
+nvcc compiles the kernels + C ABI (``csrc/s3bfs.cu``) and the query server
+(``csrc/serve.cu``), g++ the host CSR helpers (``csrc/csr_host.cpp``), all in
+parallel; then nvcc links a shared library with the CUDA runtime linked
+statically.  Objects go to ``_build/`` (ignored).
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libs3bfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = [os.path.join(CSRC, f) for f in ("s3bfs.cu", "s3bfs_device.cuh", "msbfs.cuh", "csr_host.cpp")] + \
+SOURCES = [os.path.join(CSRC, f) for f in ("s3bfs.cu", "s3bfs_device.cuh", "msbfs.cuh", "host_internal.h", "serve.cu", "serve_device.cuh", "csr_host.cpp")] + \
     [os.path.join(INCLUDE, "s3bfs.h")]
 _lock = threading.Lock()
 
@@ -45,10 +46,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         os.makedirs(BUILD, exist_ok=True)
         nv = nvcc()
         obj_cu = os.path.join(BUILD, "s3bfs.o")
+        obj_serve = os.path.join(BUILD, "serve.o")
         obj_cpp = os.path.join(BUILD, "csr_host.o")
+        nvflags = [nv, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
         cmds = [
-            [nv, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-             "-c", os.path.join(CSRC, "s3bfs.cu"), "-o", obj_cu] + (["-Xptxas", "-v"] if verbose else []),
+            nvflags + ["-c", os.path.join(CSRC, "s3bfs.cu"), "-o", obj_cu] + (["-Xptxas", "-v"] if verbose else []),
+            nvflags + ["-c", os.path.join(CSRC, "serve.cu"), "-o", obj_serve] + (["-Xptxas", "-v"] if verbose else []),
             ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-c", os.path.join(CSRC, "csr_host.cpp"), "-o",
              obj_cpp],
         ]
@@ -60,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and o:
                 print(o)
         tmp = LIB + f".tmp{os.getpid()}"
-        link = [nv, *ARCH, "-shared", "-o", tmp, obj_cu, obj_cpp]
+        link = [nv, *ARCH, "-shared", "-o", tmp, obj_cu, obj_serve, obj_cpp]
         r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")

@@ -31,7 +31,8 @@ BFS_DEBUG_STALL_BARRIER = 1
 BFS_LEVEL_FIELDS = 7
 
 EXPORTS = ("bfs_create_csr", "bfs_run", "bfs_run_batch", "bfs_destroy", "bfs_strerror", "bfs_last_error",
-           "bfs_graph_info", "bfs_run_csr_noalloc")
+           "bfs_graph_info", "bfs_run_csr_noalloc", "bfs_server_create", "bfs_server_submit", "bfs_server_poll",
+           "bfs_server_pending", "bfs_server_destroy")
 
 
 class bfs_opts(ctypes.Structure):
@@ -61,6 +62,33 @@ class bfs_stats(ctypes.Structure):
         ("per_level", ctypes.POINTER(ctypes.c_int32)),
         ("per_level_cap", ctypes.c_int32),
         ("work_edges", ctypes.c_int64),
+    ]
+
+
+class bfs_server_opts(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int32),
+        ("levels_per_launch", ctypes.c_int32),
+        ("chunk_edges", ctypes.c_int32),
+        ("cta_warps", ctypes.c_int32),
+        ("spin_limit_ms", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("arena_bytes", ctypes.c_int64),
+    ]
+
+
+class bfs_completion(ctypes.Structure):
+    _fields_ = [
+        ("tag", ctypes.c_int64),
+        ("graph", ctypes.c_int32),
+        ("src", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("num_levels", ctypes.c_int32),
+        ("reached", ctypes.c_int64),
+        ("edges_scanned", ctypes.c_int64),
+        ("t_submit_us", ctypes.c_double),
+        ("t_admit_us", ctypes.c_double),
+        ("t_done_us", ctypes.c_double),
     ]
 
 
@@ -105,6 +133,17 @@ def load():
                                    ctypes.POINTER(i32)]
     lib.bfs_run_csr_noalloc.restype = ctypes.c_int
     lib.bfs_run_csr_noalloc.argtypes = [i32, i32, i32p, i32p, i32, i32p, i32p, vp]
+    lib.bfs_server_create.restype = ctypes.c_int
+    lib.bfs_server_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(bfs_server_opts), vp,
+                                      ctypes.POINTER(vp)]
+    lib.bfs_server_submit.restype = ctypes.c_int
+    lib.bfs_server_submit.argtypes = [vp, i32, i32, i32p, i32p, ctypes.c_int64]
+    lib.bfs_server_poll.restype = ctypes.c_int
+    lib.bfs_server_poll.argtypes = [vp, ctypes.POINTER(bfs_completion), i32, ctypes.POINTER(i32)]
+    lib.bfs_server_pending.restype = ctypes.c_int
+    lib.bfs_server_pending.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.bfs_server_destroy.restype = None
+    lib.bfs_server_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -188,3 +227,38 @@ def bfs_run_csr_noalloc(n: int, nnz: int, row_ptr, col_idx, src: int, level_out,
                                     int(src), _addr(level_out, "level_out"), _addr(parent_out, "parent_out"),
                                     cuda_stream or None)
     _check(rc)
+
+
+def bfs_server_create(graphs, opts: bfs_server_opts | None = None, cuda_stream: int | None = None) -> int:
+    """``graphs``: handles from bfs_create_csr.  Returns the server handle."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(graphs))(*graphs)
+    out = ctypes.c_void_p()
+    rc = lib.bfs_server_create(arr, len(graphs), ctypes.byref(opts) if opts is not None else None,
+                               cuda_stream or None, ctypes.byref(out))
+    _check(rc)
+    return out.value
+
+
+def bfs_server_submit(s: int, graph: int, src: int, level_out=None, parent_out=None, tag: int = 0) -> None:
+    _check(load().bfs_server_submit(s, int(graph), int(src), _addr(level_out, "level_out"),
+                                    _addr(parent_out, "parent_out"), int(tag)))
+
+
+def bfs_server_poll(s: int, cap: int = 256) -> list:
+    """One scheduling round; returns the completion records it produced."""
+    buf = (bfs_completion * cap)()
+    nd = ctypes.c_int32()
+    _check(load().bfs_server_poll(s, buf, cap, ctypes.byref(nd)))
+    return [buf[i] for i in range(nd.value)]
+
+
+def bfs_server_pending(s: int) -> tuple[int, int]:
+    q, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().bfs_server_pending(s, ctypes.byref(q), ctypes.byref(r)))
+    return q.value, r.value
+
+
+def bfs_server_destroy(s: int | None) -> None:
+    if s:
+        load().bfs_server_destroy(s)

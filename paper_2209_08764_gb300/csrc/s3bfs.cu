@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "host_internal.h"
 #include "msbfs.cuh"
 #include "s3bfs.h"
 #include "s3bfs_device.cuh"
@@ -43,63 +44,7 @@ static const void* level_loop_fn(int wpc) {
 
 // a0 (Fig. 1 lines 1-8): level = parent = -1 except level[s] = 0, parent[s] =
 // s; F_0 = [s] with its row start and degree; clear the scan and barrier state.
-__global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const int n = p.n, s = p.src;
-  const bool vec = ((reinterpret_cast<uintptr_t>(p.level) | reinterpret_cast<uintptr_t>(p.parent)) & 15) == 0;
-  if (vec) {
-    int4* L4 = reinterpret_cast<int4*>(p.level);
-    int4* P4 = reinterpret_cast<int4*>(p.parent);
-    const long long n4 = n >> 2;
-    for (long long i = tid; i < n4; i += stride) {
-      int4 lv = make_int4(-1, -1, -1, -1), pv = make_int4(-1, -1, -1, -1);
-      const long long b = i << 2;
-      if (s >= b && s < b + 4) {
-        const int o = (int)(s - b);
-        if (o == 0) { lv.x = 0; pv.x = s; }
-        if (o == 1) { lv.y = 0; pv.y = s; }
-        if (o == 2) { lv.z = 0; pv.z = s; }
-        if (o == 3) { lv.w = 0; pv.w = s; }
-      }
-      L4[i] = lv;
-      P4[i] = pv;
-    }
-    for (long long v = (n4 << 2) + tid; v < n; v += stride) {
-      p.level[v] = v == s ? 0 : -1;
-      p.parent[v] = v == s ? s : -1;
-    }
-  } else {
-    for (long long v = tid; v < n; v += stride) {
-      p.level[v] = v == s ? 0 : -1;
-      p.parent[v] = v == s ? s : -1;
-    }
-  }
-  for (long long i = tid; i < p.max_chunks; i += stride) p.status[i].word = 0ull;
-  for (long long i = tid; i < ((ctas + 3) & ~3); i += stride) p.bar_arrive[i] = 0;
-  for (long long i = tid; i < (p.hub_n >> 5); i += stride) p.hub_bits[i] = 0u;
-  if (tid == 0) {
-    const int rs = p.row_ptr[s], deg = p.row_ptr[s + 1] - rs;
-    p.F[0][0] = s;
-    p.RS[0][0] = rs;
-    p.EX[0][0] = 0;
-    p.EX[0][1] = deg;
-    DevState* st = p.st;
-    st->ctrl[0].n = 1;
-    st->ctrl[0].e = deg;
-    st->ctrl[0].c = 0;
-    st->ctrl[1].n = 0;
-    st->ctrl[1].e = 0;
-    st->ctrl[1].c = 0;
-    st->err = 0;
-    st->err_where = 0;
-    st->num_levels = 0;
-    st->bar_release = 0;
-    st->reached = st->edges = st->cands = 0;
-    st->progress = 0;
-    st->resume_level = 0;
-  }
-}
+__global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) { init_traversal(p, ctas); }
 
 // The whole level loop runs in one cooperative launch (k_level_loop).  A
 // level with at most p.small_edges edges starts a streak that CTA 0 runs
@@ -148,7 +93,7 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
   if (P_l == 0) {
     if (gw == 0 && lane == 0) publish_empty_next(p, par);
   } else if (!GRID || (int)blockIdx.x * W < P_l) {
-    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
+    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0);
   }
   if (GRID) {
     if (!grid_sync(p, ++*bar)) return false;
@@ -252,7 +197,7 @@ __global__ void __launch_bounds__(W * kWarp) k_compact(Params p, int l, int e_l,
   // every thread of the CTA takes part; warps without a chunk bring 0
   const int e_begin = gw < P_l ? (int)min((long long)gw * C_l, (long long)e_l) : 0;
   const int cnt = gw < P_l ? ld_relaxed(&p.cand_cnt[gw]) : 0;
-  compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt);
+  compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, (int)blockIdx.x);
 }
 
 // CSR sanity checks that every traversal relies on (no out-of-range access):
@@ -272,76 +217,16 @@ __global__ void k_check_csr(int32_t n, int32_t nnz, const int32_t* rp, const int
 __global__ void __launch_bounds__(kThreads) k_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
                                                        const int32_t* level, const int32_t* parent,
                                                        int32_t* level_out, int32_t* parent_out) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-    const int i = __ldg(inv + v);
-    level_out[v] = level[i];
-    if (parent_out) {
-      const int q = parent[i];
-      parent_out[v] = q >= 0 ? __ldg(perm + q) : -1;
-    }
-  }
+  finalize_outputs(n, inv, perm, level, parent, level_out, parent_out);
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
-struct bfs_graph {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int32_t n = 0, nnz = 0;
-  int sms = 0;
-  int ctas = 0;   // G
-  int warps = 0;  // P
-  int wpc = 32;   // warps per CTA of the level loop (8 or 32)
-  int grain = 64;
-  int persistent = 1;
-  int work_insensitive = 0;
-  int debug_flags = 0;
-  long long spin_ns = 1000000000ll;
-  int small_edges = -1;  // resolved at create: 256 edges per warp of one CTA
-  int32_t lvl_cap = 0;
-  int hub_n = 0;         // vertices [0, hub_n) have visited bits in shared memory
-  bool relabel = false;  // internal ids are degree-descending (hubs first)
-  std::vector<int32_t> h_inv;
-  int32_t *d_perm = nullptr, *d_inv = nullptr;
-  uint32_t* d_hub_bits = nullptr;
-  int32_t *d_out_level = nullptr, *d_out_parent = nullptr;  // translated outputs for host buffers
-  int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr;
-  int32_t *d_level = nullptr, *d_parent = nullptr;
-  int32_t *d_F[2] = {nullptr, nullptr}, *d_RS[2] = {nullptr, nullptr}, *d_EX[2] = {nullptr, nullptr};
-  int2* d_cand = nullptr;
-  int32_t* d_cand_aux = nullptr;
-  int32_t* d_cand_cnt = nullptr;
-  ChunkStatus* d_status = nullptr;
-  int32_t *d_arrive = nullptr, *d_smid = nullptr;
-  DevState* d_st = nullptr;
-  int32_t* d_lvl = nullptr;
-  DevState* h_st = nullptr;  // pinned
-  int32_t* h_smid = nullptr; // pinned
-  int32_t* h_ctrl = nullptr; // pinned, launch-per-phase mode
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  std::vector<void*> allocs;
-  // multi-source (bitmask) batches, allocated at the first batch
-  bool symmetric = false;
-  int batch_bitmask = 0;
-  bool ms_ready = false;
-  int ms_ctas = 0;
-  unsigned long long *d_seen = nullptr, *d_fr[2] = {nullptr, nullptr};
-  int32_t *d_heavy = nullptr, *d_huge = nullptr;
-  int32_t n_heavy = 0, n_huge = 0;
-  unsigned long long *d_block_or = nullptr, *d_level_bits = nullptr;
-  long long* d_block_edges = nullptr;
-  long long* d_counts = nullptr;
-  int32_t* d_groups = nullptr;  // vs[64], src_int[64], src_out[64]
-  unsigned long long* d_masks = nullptr;
-  int32_t *d_stage_level = nullptr, *d_stage_parent = nullptr;  // 64 x n, for host outputs
-};
+thread_local char g_last_error[512] = "";
 
-static thread_local char g_last_error[512] = "";
-
-static int fail(int code, const char* fmt, ...) {
+int fail(int code, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
@@ -349,28 +234,7 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-#define CUDA_TRY(expr)                                                                          \
-  do {                                                                                          \
-    cudaError_t e_ = (expr);                                                                    \
-    if (e_ != cudaSuccess) return fail(BFS_E_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
-                                       __FILE__, __LINE__);                                     \
-  } while (0)
-
-template <class T>
-static int dalloc(bfs_graph* g, T** p, size_t count) {
-  void* q = nullptr;
-  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(BFS_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
-  }
-  g->allocs.push_back(q);
-  *p = static_cast<T*>(q);
-  return BFS_OK;
-}
-
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -542,7 +406,8 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   g->wpc = cw ? cw : (g->hub_n > 0 ? 32 : 8);
   // persistent grid: every CTA that fits next to the shared-memory bits
   const void* loop_fn = level_loop_fn(g->wpc);
-  CUDA_TRY(cudaFuncSetAttribute(loop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(g->hub_n)));
+  // the attribute is per kernel, shared by every graph: set it to the largest size any graph uses
+  CUDA_TRY(cudaFuncSetAttribute(loop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(kHubMax)));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_fn, g->wpc * kWarp, loop_smem(g->hub_n)));
   if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");

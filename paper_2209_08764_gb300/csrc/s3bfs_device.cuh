@@ -376,7 +376,7 @@ __device__ __forceinline__ int emit(int2* out, int cnt, bool k, int v, int u, in
 // s_hub / hub_lim: visited bits of vertices [0, hub_lim) in shared memory, a
 // snapshot taken at the start of the level (hub_lim = 0: none).  A set bit
 // means the vertex already has a level, so its level[] test is skipped.
-__device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, int e_begin, int e_end,
+__device__ inline int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, int e_begin, int e_end,
                              int2* out, const uint32_t* s_hub, int hub_lim) {
   const int lane = threadIdx.x & (kWarp - 1);
   // (selects, not p.EX[par]: a runtime index into the parameter block would
@@ -534,14 +534,15 @@ __device__ int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, 
 // next level's n and e.  Returns false (in every thread) if a wait ran out.
 constexpr int kCompactR = S3BFS_CR;
 
+// b: rank of this CTA among the CTAs that hold the level's chunks (the scan
+// runs over ranks 0 .. (P_l - 1) / W).
 template <int W>  // warps per CTA
-__device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt) {
+__device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt, int b) {
   __shared__ int sK[W], sD[W], sC[W];
   __shared__ int sRed[3][W];
   __shared__ int sPre[3];
   const int lane = threadIdx.x & (kWarp - 1);
   const int wib = threadIdx.x >> 5;
-  const int b = blockIdx.x;
   const int np = par ^ 1;
   int* Fn = np ? p.F[1] : p.F[0];
   int* RSn = np ? p.RS[1] : p.RS[0];
@@ -761,6 +762,81 @@ __device__ __forceinline__ void record_level(const Params& p, int l, int n_l, in
     r[4] = 0;
     r[5] = 0;
     r[6] = 0;
+  }
+}
+
+// a0 (Fig. 1 lines 1-8): level = parent = -1 except level[s] = 0, parent[s] =
+// s; F_0 = [s] with its row start and degree; clear the scan and barrier
+// state (ctas arrival words; none if 0) and the visited bits.  Grid-stride.
+__device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int n = p.n, s = p.src;
+  const bool vec = ((reinterpret_cast<uintptr_t>(p.level) | reinterpret_cast<uintptr_t>(p.parent)) & 15) == 0;
+  if (vec) {
+    int4* L4 = reinterpret_cast<int4*>(p.level);
+    int4* P4 = reinterpret_cast<int4*>(p.parent);
+    const long long n4 = n >> 2;
+    for (long long i = tid; i < n4; i += stride) {
+      int4 lv = make_int4(-1, -1, -1, -1), pv = make_int4(-1, -1, -1, -1);
+      const long long b = i << 2;
+      if (s >= b && s < b + 4) {
+        const int o = (int)(s - b);
+        if (o == 0) { lv.x = 0; pv.x = s; }
+        if (o == 1) { lv.y = 0; pv.y = s; }
+        if (o == 2) { lv.z = 0; pv.z = s; }
+        if (o == 3) { lv.w = 0; pv.w = s; }
+      }
+      L4[i] = lv;
+      P4[i] = pv;
+    }
+    for (long long v = (n4 << 2) + tid; v < n; v += stride) {
+      p.level[v] = v == s ? 0 : -1;
+      p.parent[v] = v == s ? s : -1;
+    }
+  } else {
+    for (long long v = tid; v < n; v += stride) {
+      p.level[v] = v == s ? 0 : -1;
+      p.parent[v] = v == s ? s : -1;
+    }
+  }
+  for (long long i = tid; i < p.max_chunks; i += stride) p.status[i].word = 0ull;
+  for (long long i = tid; i < ((ctas + 3) & ~3); i += stride) p.bar_arrive[i] = 0;
+  for (long long i = tid; i < (p.hub_n >> 5); i += stride) p.hub_bits[i] = 0u;
+  if (tid == 0) {
+    const int rs = p.row_ptr[s], deg = p.row_ptr[s + 1] - rs;
+    p.F[0][0] = s;
+    p.RS[0][0] = rs;
+    p.EX[0][0] = 0;
+    p.EX[0][1] = deg;
+    DevState* st = p.st;
+    st->ctrl[0].n = 1;
+    st->ctrl[0].e = deg;
+    st->ctrl[0].c = 0;
+    st->ctrl[1].n = 0;
+    st->ctrl[1].e = 0;
+    st->ctrl[1].c = 0;
+    st->err = 0;
+    st->err_where = 0;
+    st->num_levels = 0;
+    st->bar_release = 0;
+    st->reached = st->edges = st->cands = 0;
+    st->progress = 0;
+    st->resume_level = 0;
+  }
+}
+
+__device__ __forceinline__ void finalize_outputs(int32_t n, const int32_t* inv, const int32_t* perm,
+                                                 const int32_t* level, const int32_t* parent, int32_t* level_out,
+                                                 int32_t* parent_out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const int i = __ldg(inv + v);
+    level_out[v] = level[i];
+    if (parent_out) {
+      const int q = parent[i];
+      parent_out[v] = q >= 0 ? __ldg(perm + q) : -1;
+    }
   }
 }
 

@@ -1,0 +1,147 @@
+// Serving: many single-source traversals, possibly on different graphs, in
+// one cooperative launch, advanced level by level.
+//
+// Every running query owns a slot: the Params of its traversal (its graph's
+// CSR, its own level/parent/frontier/candidate buffers and control block).
+// At every level all CTAs compute the same split of the grid among the
+// running queries -- each gets at least one CTA and the rest in proportion to
+// its level's edge count -- and each CTA runs the S3BFS level step (explore,
+// grid barrier, compact with a scan over that query's CTAs, grid barrier) for
+// its query.  A launch returns after a bounded number of levels or as soon as
+// a query finishes, so that the host can retire finished queries and admit
+// new ones between launches (continuous batching at level granularity).
+// Batching queries is not in the paper; each query is Parallel-BFS(s, P)
+// (Fig. 1) unchanged.
+#pragma once
+
+#include "s3bfs_device.cuh"
+
+namespace s3bfs {
+
+constexpr int kMaxSlots = 128;
+
+struct SlotDev {
+  Params p;            // the query's traversal
+  int32_t level;       // its current level
+  int32_t active;      // 1 while it runs, 0 when done (or failed)
+  int32_t num_levels;  // levels done
+  int32_t pad;
+  long long reached, edges, cands;
+};
+
+struct ServeParams {
+  SlotDev* slots;
+  int32_t nslots;
+  int32_t max_levels;  // levels per launch
+  int32_t grain;
+  int32_t* finished;   // set when a query finished during this launch
+  // grid barrier state of the server
+  DevState* st;
+  int32_t* bar_arrive;
+  long long spin_ns;
+  int32_t debug_flags;
+};
+
+// Split of gridDim.x CTAs among the running queries: every query with a
+// non-empty frontier gets one CTA plus a share of the rest proportional to
+// its level's edge count.  Whole CTA (the slot states are read in parallel,
+// one thread per slot); thread 0 then sets q (-1: idle CTA, -2: nothing
+// runs), the CTA's rank in its query's group and the group size.
+__device__ __forceinline__ void serve_assign(const ServeParams& sp, long long* s_w, int* q_out, int* rank_out,
+                                             int* size_out) {
+  const int t = threadIdx.x;
+  if (t < sp.nslots) {
+    const SlotDev& sd = sp.slots[t];
+    long long w = 0;
+    if (ld_relaxed(&sd.active)) {
+      const int l = ld_relaxed(&sd.level);
+      const int n = ld_relaxed(&sd.p.st->ctrl[l & 1].n);
+      if (n > 0) w = max(ld_relaxed(&sd.p.st->ctrl[l & 1].e), 1);
+    }
+    s_w[t] = w;
+  }
+  __syncthreads();
+  if (t == 0) {
+    const int G = gridDim.x;
+    long long wsum = 0;
+    int A = 0;
+    for (int q = 0; q < sp.nslots; ++q) {
+      wsum += s_w[q];
+      A += s_w[q] > 0;
+    }
+    *q_out = A == 0 ? -2 : -1;
+    const long long spare = G > A ? G - A : 0;
+    int start = 0;
+    for (int q = 0; q < sp.nslots && A > 0; ++q) {
+      if (s_w[q] == 0) continue;
+      const int g = 1 + (int)(spare * s_w[q] / wsum);
+      if ((int)blockIdx.x >= start && (int)blockIdx.x < start + g) {
+        *q_out = q;
+        *rank_out = (int)blockIdx.x - start;
+        *size_out = g;
+      }
+      start += g;
+    }
+  }
+}
+
+// One launch: up to sp.max_levels levels of every running query.
+template <int W>
+__global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParams sp) {
+  __shared__ int s_q, s_rank, s_size;
+  __shared__ long long s_w[kMaxSlots];
+  const int wib = threadIdx.x >> 5;
+  int bar = 0;
+  for (int it = 0; it < sp.max_levels; ++it) {
+    serve_assign(sp, s_w, &s_q, &s_rank, &s_size);
+    __syncthreads();
+    const int q = s_q, rank = s_rank, gsize = s_size;
+    __syncthreads();
+    if (q == -2) break;  // same decision in every CTA: they read the same slot states
+    SlotDev* sd = q >= 0 ? sp.slots + q : nullptr;
+    int l = 0, par = 0, n_l = 0, e_l = 0, P_l = 0, C_l = 0, cnt = 0, e_begin = 0;
+    if (sd) {
+      const Params& p = sd->p;
+      l = ld_relaxed(&sd->level);
+      par = l & 1;
+      n_l = ld_relaxed(&p.st->ctrl[par].n);
+      e_l = ld_relaxed(&p.st->ctrl[par].e);
+      level_sizing(e_l, gsize * W, sp.grain, 0, &P_l, &C_l);
+      const int gw = rank * W + wib;
+      if (gw < P_l) {
+        const long long eb = (long long)gw * C_l;
+        e_begin = (int)min(eb, (long long)e_l);
+        const int e_end = (int)min(eb + C_l, (long long)e_l);
+        if (e_begin < e_end)
+          cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
+      }
+    }
+    if (!grid_sync(sp, ++bar)) break;
+    if (sd) {
+      const Params& p = sd->p;
+      if (P_l == 0) {
+        if (rank == 0 && threadIdx.x == 0) publish_empty_next(p, par);
+      } else if (rank * W < P_l) {
+        compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, rank);
+      }
+      // the CTA that published the next level's sizes updates the slot
+      const int last = P_l == 0 ? 0 : (P_l - 1) / W;
+      if (rank == last && threadIdx.x == 0) {
+        const int n_next = ld_relaxed(&p.st->ctrl[par ^ 1].n);
+        sd->reached += n_l;
+        sd->edges += e_l;
+        sd->cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+        sd->num_levels = l + 1;
+        st_relaxed(&sd->level, l + 1);
+        if (n_next <= 0 || ld_relaxed(&p.st->err) != 0) {
+          st_relaxed(&sd->active, 0);
+          st_relaxed(sp.finished, 1);
+        }
+      }
+    }
+    if (!grid_sync(sp, ++bar)) break;
+    if (ld_relaxed(sp.finished) != 0) break;  // retire and admit before going on
+  }
+}
+
+}  // namespace s3bfs

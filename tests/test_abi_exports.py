@@ -57,3 +57,9 @@ def test_struct_layout_matches_header():
     assert B.bfs_stats.per_level.offset == 40
     assert B.bfs_stats.work_edges.offset == 56
     assert ctypes.sizeof(B.bfs_stats) == 64
+
+
+def test_server_struct_layout():
+    assert ctypes.sizeof(B.bfs_server_opts) == 32
+    assert B.bfs_completion.t_submit_us.offset == 40
+    assert ctypes.sizeof(B.bfs_completion) == 64

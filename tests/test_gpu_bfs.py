@@ -415,3 +415,19 @@ def test_batch_bitmask_off_and_asymmetric_rejected():
     with pytest.raises(B.BFSError) as e:
         B.bfs_create_csr(5, len(ci2), rp2, ci2, B.BFS_VALIDATE | B.BFS_SYMMETRIC)
     assert e.value.code == B.BFS_E_INVAL
+
+
+def test_graphs_of_different_sizes_coexist():
+    """Several graphs alive at once, used in an order different from their
+    creation (per-kernel launch attributes must suit all of them)."""
+    pool = [graphgen.rmat(14, 16, seed=6), graphgen.rmat(10, 16, seed=2), graphgen.grid(40, 40, 0.0),
+            graphgen.from_edges(50, [(i, i + 1) for i in range(49)])]
+    devs = [Dev(rp, ci, relabel=1 if i == 0 else 0) for i, (rp, ci) in enumerate(pool)]
+    try:
+        for d in reversed(devs):
+            check_against_oracle(d, 0)
+        for d in devs:
+            check_against_oracle(d, 1)
+    finally:
+        for d in devs:
+            d.close()
