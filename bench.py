@@ -51,7 +51,8 @@ def make_graph(w):
 
 
 def sources_for(w, rp, rank):
-    src = graphgen.sample_sources(rp, w["sources"], seed=w["src_seed"] + 1000 * rank)
+    from paper_2209_08764_gb300.replicas import rank_source_seed
+    src = graphgen.sample_sources(rp, w["sources"], seed=rank_source_seed(w["src_seed"], rank))
     if w["kind"] == "grid" and rank == 0:
         src = np.concatenate([[0], src[:-1]]).astype(np.int32)   # the corner: maximum depth
     return src
@@ -200,7 +201,7 @@ def cpu_baseline(w, rp, ci, srcs, budget_s):
             "sample": f"first {k} of the {len(srcs)} sources, one traversal each ({t:.1f} s)"}
 
 
-def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev):
+def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas):
     """One step = one bfs_run_batch over all sources (groups of 64 share a
     bitmask traversal); compared with the same sources run one at a time."""
     n, nnz = len(rp) - 1, len(ci)
@@ -233,12 +234,9 @@ def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    gteps = edges_per_step * args.steps * ws / (ms_max / 1e3) / 1e9
+    ms_max, total_edges = replicas.aggregate(dist, ms, edges_per_step * args.steps,
+                                             torch.device("cuda", dev) if dist else None)
+    gteps = total_edges / (ms_max / 1e3) / 1e9
     # the same sources one at a time through bfs_run (single-source S3BFS)
     lv = torch.empty(n, dtype=torch.int32, device=dev)
     pa = torch.empty(n, dtype=torch.int32, device=dev)
@@ -424,6 +422,7 @@ def main():
 
     import torch
     from paper_2209_08764_gb300 import binding as B
+    from paper_2209_08764_gb300 import replicas
 
     if args.serve:
         run_serve_mode(args, B, torch)
@@ -443,7 +442,7 @@ def main():
     n, nnz = len(rp) - 1, len(ci)
     srcs = sources_for(w, rp, rank)
     if args.batch:
-        run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev)
+        run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas)
         return
     deg = np.diff(rp.astype(np.int64))
     stream = torch.cuda.current_stream()
@@ -494,12 +493,8 @@ def main():
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    total_edges = edges_per_step * args.steps * ws
+    ms_max, total_edges = replicas.aggregate(dist, ms, edges_per_step * args.steps,
+                                             torch.device("cuda", dev) if dist else None)
     gteps = total_edges / (ms_max / 1e3) / 1e9
 
     # roofline of the dominant kernel (the persistent level loop), byte model:
