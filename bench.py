@@ -403,6 +403,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dump", default="", help="write per-traversal records of the timed steps (JSON) here")
     ap.add_argument("--levels", action="store_true", help="add the per-level statistics of the first source")
+    ap.add_argument("--direction", type=int, default=0,
+                    help="1: direction-optimising traversal (bottom-up levels) as the measured line")
+    ap.add_argument("--with-do", type=int, default=1,
+                    help="1 (default): add a direction-optimising run of the same sources to the top-down line")
     ap.add_argument("--batch", action="store_true",
                     help="all sources of a step in one bfs_run_batch call (64-source bitmask traversal)")
     ap.add_argument("--no-parents", action="store_true", help="levels only (batch mode)")
@@ -444,6 +448,50 @@ def main():
     if args.batch:
         run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas)
         return
+    line = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, args.direction)
+    if rank == 0 and not args.direction and args.with_do and w["kind"] != "grid":
+        # the same sources with direction-optimising levels (bottom-up where the
+        # frontier is large); the headline value stays the top-down level step
+        do = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, 1, summary=True)
+        do["speedup_vs_top_down"] = round(do["value"] / line["value"], 3)
+        line["direction_optimising"] = do
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, rp, ci, srcs, args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def level_bytes(n, rows):
+    """Algorithmic bytes of one traversal's level loop from its per-level
+    records (n_l, e_l, c_l, ..., direction, work).  Top-down level: 8 per
+    edge scanned (col_idx + level test) + 32 per frontier vertex + 28 per
+    candidate.  Bottom-up level: 4 n (visited test of every vertex) + 8 per
+    unvisited vertex (row bounds) + 8 per examined entry (col_idx + frontier
+    bit test) + n / 8 (next frontier bitmap) + 36 per vertex found (level,
+    parent, candidate pair and its compaction), plus 4 n + n / 8 when the
+    frontier bitmap is first built from the level array."""
+    total = 0.0
+    visited = 0
+    prev_dir = 0
+    for r in rows:
+        n_l, e_l, c_l, direction, work = int(r[0]), int(r[1]), int(r[2]), int(r[7]), int(r[8])
+        visited += n_l
+        if direction == 0:
+            total += 8 * e_l + 32 * n_l + 28 * c_l
+        else:
+            total += 4 * n + 8 * (n - visited) + 8 * work + n / 8 + 36 * c_l
+            if prev_dir == 0:
+                total += 4 * n + n / 8
+        prev_dir = direction
+    return total
+
+
+def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, direction, summary=False):
+    """Single-source traversals of every source, K timed steps: the bench line
+    (or, with summary, its compact form for the direction-optimising run)."""
+    n, nnz = len(rp) - 1, len(ci)
     deg = np.diff(rp.astype(np.int64))
     stream = torch.cuda.current_stream()
     opts = B.bfs_opts()
@@ -454,29 +502,50 @@ def main():
     opts.relabel = args.relabel
     opts.small_level_edges = args.small_level_edges
     opts.cta_warps = args.cta_warps
-    g = B.bfs_create_csr(n, nnz, rp, ci, B.BFS_VALIDATE, opts, stream.cuda_stream)
+    opts.direction = direction
+    # top-down: the CSR is checked on the host (BFS_VALIDATE).  The
+    # direction-optimising graph declares BFS_SYMMETRIC without that (slow)
+    # host check: the generators' output is symmetric and simple, which the
+    # CPU tests of graphgen pin.
+    flags = B.BFS_SYMMETRIC if direction else B.BFS_VALIDATE
+    t_create = time.perf_counter()
+    g = B.bfs_create_csr(n, nnz, rp, ci, flags, opts, stream.cuda_stream)
+    t_create = time.perf_counter() - t_create
     info = B.bfs_graph_info(g)
     level = torch.empty(n, dtype=torch.int32, device=dev)
     parent = torch.empty(n, dtype=torch.int32, device=dev)
     st = B.bfs_stats()
 
-    # traversed edges per source (Graph500 count), from the reached set of each traversal
     def step(record):
         out = []
         for s in srcs:
             B.bfs_run(g, int(s), level, parent, st)
             if record is not None:
                 out.append((st.ms_level_step, st.ms_total, st.reached, st.edges_scanned, st.candidates,
-                            st.num_levels, int(s)))
+                            st.num_levels, int(s), st.launches, st.work_edges))
         return out
 
     for _ in range(args.warmup):
         step(None)
-    # traversed-edge count of each source (the level array of the warm-up is exact)
-    teps_edges = []
+    # per source: traversed edges (Graph500 count: half the degree sum of the
+    # reached vertices) and the algorithmic bytes of its level loop, from one
+    # untimed run with per-level records (levels, directions and work are the
+    # same in every run of a source)
+    cap = 1 << 16
+    buf = (ctypes.c_int32 * (cap * B.BFS_LEVEL_FIELDS))()
+    st2 = B.bfs_stats()
+    st2.per_level = ctypes.cast(buf, ctypes.POINTER(ctypes.c_int32))
+    st2.per_level_cap = cap
+    teps_edges, src_bytes, first_rows, bu_levels = [], [], None, []
     for s in srcs:
-        B.bfs_run(g, int(s), level, parent, None)
+        B.bfs_run(g, int(s), level, parent, st2)
         teps_edges.append(int(deg[(level >= 0).cpu().numpy()].sum() // 2))
+        L = min(st2.num_levels, cap)
+        rows = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS).copy()
+        src_bytes.append(level_bytes(n, rows) if L == st2.num_levels else np.nan)
+        bu_levels.append(int((rows[:, 7] == 1).sum()))
+        if first_rows is None:
+            first_rows = rows
     edges_per_step = sum(teps_edges)
 
     if dist:
@@ -497,19 +566,29 @@ def main():
                                              torch.device("cuda", dev) if dist else None)
     gteps = total_edges / (ms_max / 1e3) / 1e9
 
-    # roofline of the dominant kernel (the persistent level loop), byte model:
-    # 8 m_r + 32 n_r + 28 C_tot per traversal (level step; init's 8 n excluded)
+    # roofline of the dominant kernel (the persistent level loop): algorithmic
+    # bytes of each traversal's level loop / its device time
     recs = np.array(recs, dtype=np.float64)
     ms_loop = recs[:, 0]
-    bytes_loop = 8 * recs[:, 3] + 32 * recs[:, 2] + 28 * recs[:, 4]
+    bytes_loop = np.tile(np.array(src_bytes, dtype=np.float64), args.steps)
     achieved = bytes_loop.sum() / (ms_loop.sum() / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload) if not direction else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_level_loop", "algorithmic_bytes_per_launch": float(bytes_loop.mean()),
                 "avg_launch_ms": float(ms_loop.mean())}
     hmean = len(ms_loop) / np.sum(ms_loop / 1e3 / np.tile(teps_edges, args.steps)) / 1e9
+    launches = int(recs[:, 7].sum())
+    if summary:
+        B.bfs_destroy(g)
+        return {"value": round(gteps, 3), "unit": "GTEPS", "ms_per_step": ms_max / args.steps,
+                "ms_level_step_median": float(np.median(ms_loop)), "roofline": roofline,
+                "bottom_up_levels_median": float(np.median(bu_levels)),
+                "work_edges_per_traversal": float(recs[:, 8].mean()),
+                "edges_scanned_per_traversal": float(recs[:, 3].mean()),
+                "gpu_launches": launches, "clocks": clk.summary(),
+                "options": {"alpha": 15, "beta": 18}, "create_s": round(t_create, 2)}
 
     # end to end through the C ABI with pinned host outputs (copies inside the timed region)
     e2e = None
@@ -528,28 +607,26 @@ def main():
 
     per_level = None
     if args.levels:
-        cap = 1 << 16
-        buf = (ctypes.c_int32 * (cap * B.BFS_LEVEL_FIELDS))()
-        st2 = B.bfs_stats()
-        st2.per_level = ctypes.cast(buf, ctypes.POINTER(ctypes.c_int32))
-        st2.per_level_cap = cap
-        B.bfs_run(g, int(srcs[0]), level, parent, st2)
-        L = min(st2.num_levels, cap)
-        rows = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS)
-        per_level = {"src": int(srcs[0]), "fields": ["n_l", "e_l", "c_l", "active_warps", "active_sms", "ns", "ns_explore"],
-                     "rows": rows.tolist() if L <= 64 else rows[:64].tolist(), "levels": L,
+        rows = first_rows
+        per_level = {"src": int(srcs[0]), "fields": ["n_l", "e_l", "c_l", "active_warps", "active_sms", "ns",
+                                                     "ns_explore", "direction", "work"],
+                     "rows": rows.tolist() if len(rows) <= 64 else rows[:64].tolist(), "levels": len(rows),
                      "ns_total": int(rows[:, 5].sum())}
     if args.dump and rank == 0:
         with open(args.dump, "w") as f:
             json.dump([{"src": int(r[6]), "ms_level_step": r[0], "ms_total": r[1], "reached": int(r[2]),
                         "edges_scanned": int(r[3]), "candidates": int(r[4]), "levels": int(r[5]),
-                        "algorithmic_bytes": float(8 * r[3] + 32 * r[2] + 28 * r[4])} for r in recs.tolist()], f)
+                        "work_edges": int(r[8]), "algorithmic_bytes": float(b)}
+                       for r, b in zip(recs.tolist(), bytes_loop.tolist())], f)
+    line = None
     if rank == 0:
+        config = config_of(args.workload, w, rp, ci)
+        config["direction"] = "direction-optimising (alpha 15, beta 18)" if direction else "top-down (S3BFS level step)"
         line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": config_of(args.workload, w, rp, ci), "roofline": roofline,
-                "clocks": clk.summary(), "gpu_launches": int(2 * len(srcs) * args.steps),
+                "config": config, "roofline": roofline,
+                "clocks": clk.summary(), "gpu_launches": launches,
                 "harmonic_mean_gteps_level_step": float(hmean),
                 "ms_level_step_median": float(np.median(ms_loop)),
                 "levels_median": float(np.median(recs[:, 5])),
@@ -558,12 +635,8 @@ def main():
             line["e2e"] = e2e
         if per_level:
             line["per_level"] = per_level
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, rp, ci, srcs, args.cpu_budget)
-        print(json.dumps(line), flush=True)
     B.bfs_destroy(g)
-    if dist:
-        dist.destroy_process_group()
+    return line
 
 
 if __name__ == "__main__":

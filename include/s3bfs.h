@@ -78,10 +78,24 @@ typedef struct bfs_opts {
   int32_t cta_warps;        /* warps per CTA of the level loop: 32 (one CTA per SM,
                                one copy of the shared-memory visited bits) or 8;
                                0 = 32 when visited bits are kept, else 8 */
+  int32_t direction;        /* 0 (default): every level top-down, the S3BFS level step.
+                               1: direction-optimising (needs BFS_SYMMETRIC, else
+                               bfs_create_csr fails with BFS_E_INVAL): a level whose
+                               frontier edges exceed m_u / do_alpha (m_u = degree sum
+                               of the unvisited vertices) runs bottom-up -- every
+                               unvisited vertex looks for a parent in the frontier --
+                               and the traversal turns top-down again once the
+                               frontier shrinks below n / do_beta (Beamer et al.,
+                               SC 2012; the paper names bottom-up steps as compatible
+                               with S3BFS in its conclusion).  Levels are the same;
+                               parents are another valid BFS tree.  Persistent loop
+                               only: with persistent = -1 every level is top-down */
+  int32_t do_alpha;         /* 0 = 15 */
+  int32_t do_beta;          /* 0 = 18 */
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */
-#define BFS_LEVEL_FIELDS 7
+#define BFS_LEVEL_FIELDS 9
 /* [0] n_l          frontier size (vertices at distance l)
  * [1] e_l          edges the level scans (sum of frontier out-degrees)
  * [2] c_l          candidates emitted by the explore step (n_{l+1} <= c_l <= e_l)
@@ -89,7 +103,10 @@ typedef struct bfs_opts {
  * [4] active_sms   distinct SMs hosting those warps (-1 with one launch per phase)
  * [5] ns           device time of the level, explore to the end of the compact
  *                  barrier, from the global timer (-1 with one launch per phase)
- * [6] ns_explore   the part of [5] up to the end of the explore barrier */
+ * [6] ns_explore   the part of [5] up to the end of the explore barrier
+ *                  (bottom-up: of the neighbour scan)
+ * [7] direction    0 top-down, 1 bottom-up
+ * [8] work         neighbour entries examined (top-down: e_l) */
 
 /* Statistics of one traversal (all optional). */
 typedef struct bfs_stats {
@@ -102,8 +119,10 @@ typedef struct bfs_stats {
   float ms_total;         /* device time including initialisation */
   int32_t *per_level;     /* in: optional host buffer of per_level_cap * BFS_LEVEL_FIELDS int32 */
   int32_t per_level_cap;  /* in: capacity in levels; levels beyond it are counted, not recorded */
-  int64_t work_edges;     /* neighbour entries the kernels read: edges_scanned for one source;
-                             for a bitmask batch group, the pulled entries of all its levels */
+  int32_t launches;       /* kernels the call launched (for a bitmask batch group: the group's) */
+  int64_t work_edges;     /* neighbour entries the kernels examined: edges_scanned for a
+                             top-down traversal, fewer with bottom-up levels; for a bitmask
+                             batch group, the pulled entries of all its levels */
 } bfs_stats;
 
 typedef struct bfs_graph bfs_graph; /* opaque; owned by the library */

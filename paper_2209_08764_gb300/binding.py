@@ -28,7 +28,7 @@ BFS_DEDUP = 4
 BFS_SYMMETRIC = 8
 
 BFS_DEBUG_STALL_BARRIER = 1
-BFS_LEVEL_FIELDS = 7
+BFS_LEVEL_FIELDS = 9
 
 EXPORTS = ("bfs_create_csr", "bfs_run", "bfs_run_batch", "bfs_destroy", "bfs_strerror", "bfs_last_error",
            "bfs_graph_info", "bfs_run_csr_noalloc", "bfs_server_create", "bfs_server_submit", "bfs_server_poll",
@@ -47,6 +47,9 @@ class bfs_opts(ctypes.Structure):
         ("batch_bitmask", ctypes.c_int32),
         ("small_level_edges", ctypes.c_int32),
         ("cta_warps", ctypes.c_int32),
+        ("direction", ctypes.c_int32),
+        ("do_alpha", ctypes.c_int32),
+        ("do_beta", ctypes.c_int32),
     ]
 
 
@@ -61,6 +64,7 @@ class bfs_stats(ctypes.Structure):
         ("ms_total", ctypes.c_float),
         ("per_level", ctypes.POINTER(ctypes.c_int32)),
         ("per_level_cap", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
         ("work_edges", ctypes.c_int64),
     ]
 

@@ -81,9 +81,10 @@ double s3bfs_host_top_degree_share(int32_t n, const int32_t* rp, int32_t top) {
 
 // Degree-descending renumbering (ties by id): perm[i] is the caller's id of
 // internal vertex i, inv[v] the internal id of v.  The renumbered CSR lists
-// internal rows in order, with every neighbour translated through inv.
-// Returns 0, or -1 if host memory ran out.
-int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* perm,
+// internal rows in order, with every neighbour translated through inv; with
+// sort_rows every row is sorted (highest-degree neighbours first, which a
+// bottom-up level tries first).  Returns 0, or -1 if host memory ran out.
+int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, bool sort_rows, std::vector<int32_t>* perm,
                        std::vector<int32_t>* inv, std::vector<int32_t>* rp_out, std::vector<int32_t>* ci_out) {
   try {
     int32_t maxd = 0;
@@ -104,7 +105,9 @@ int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vec
     int64_t w = 0;
     for (int32_t i = 0; i < n; ++i) {
       const int32_t v = (*perm)[(size_t)i];
+      const int64_t w0 = w;
       for (int32_t e = rp[v]; e < rp[v + 1]; ++e) (*ci_out)[(size_t)w++] = (*inv)[(size_t)ci[e]];
+      if (sort_rows) std::sort(ci_out->begin() + w0, ci_out->begin() + w);
       (*rp_out)[(size_t)i + 1] = (int32_t)w;
     }
   } catch (const std::bad_alloc&) {

@@ -29,6 +29,11 @@ struct bfs_graph {
   int debug_flags = 0;
   long long spin_ns = 1000000000ll;
   int small_edges = -1;  // resolved at create: 256 edges per warp of one CTA
+  int launches = 0;      // kernels launched by the current call
+  int direction = 0;     // 1: direction-optimising (bottom-up levels)
+  int alpha = 15, beta = 18;
+  int32_t nwords = 0;    // words of a frontier bitmap
+  uint32_t* d_fb[2] = {nullptr, nullptr};
   int32_t lvl_cap = 0;
   int hub_n = 0;         // vertices [0, hub_n) have visited bits in shared memory
   bool relabel = false;  // internal ids are degree-descending (hubs first)

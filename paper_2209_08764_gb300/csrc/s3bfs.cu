@@ -25,7 +25,7 @@ int s3bfs_host_dedup(int32_t n, const int32_t* rp, const int32_t* ci, std::vecto
                      std::vector<int32_t>* ci_out);
 double s3bfs_host_top_degree_share(int32_t n, const int32_t* rp, int32_t top);
 int s3bfs_host_is_symmetric(int32_t n, const int32_t* rp, const int32_t* ci);
-int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, std::vector<int32_t>* perm,
+int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, bool sort_rows, std::vector<int32_t>* perm,
                        std::vector<int32_t>* inv, std::vector<int32_t>* rp_out, std::vector<int32_t>* ci_out);
 
 // dynamic shared memory of the level loop: the visited bits
@@ -76,11 +76,12 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
   }
   // big level: take the visited-bits snapshot into shared memory
   const int hub_lim = (GRID && p.hub_n > 0 && e_l >= p.hub_n) ? load_hub_bits(p, s_hub) : 0;
-  int cnt = 0, e_begin = 0;
+  int cnt = 0, e_begin = 0, work = 0;
   if (gw < P_l) {
     const long long eb = (long long)gw * C_l;
     e_begin = (int)min(eb, (long long)e_l);
     const int e_end = (int)min(eb + C_l, (long long)e_l);
+    work = e_end - e_begin;
     if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
   }
   if (GRID) {
@@ -93,7 +94,7 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
   if (P_l == 0) {
     if (gw == 0 && lane == 0) publish_empty_next(p, par);
   } else if (!GRID || (int)blockIdx.x * W < P_l) {
-    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0);
+    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0, work);
   }
   if (GRID) {
     if (!grid_sync(p, ++*bar)) return false;
@@ -105,6 +106,51 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
   }
   if (leader) {
     acc[2] += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+    acc[3] += ld_relaxed(&p.st->ctrl[par ^ 1].w);
+    if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
+  }
+  return true;
+}
+
+// One bottom-up level on the whole grid (direction-optimising traversal of a
+// symmetric graph).  If the level before ran top-down, the frontier bitmap
+// is first built from the level array (grid barrier).  Every warp then scans
+// its share of the unvisited vertices for a parent in the frontier (grid
+// barrier), and the standard compaction turns the new vertices into the next
+// frontier record and publishes its sizes (grid barrier).  Warp gw's
+// candidates go to its own region of the candidate buffer, room for 32
+// vertices per word it owns.
+template <int W>
+__device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, int* bar, long long* acc) {
+  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
+  const int P = gridDim.x * W;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const int par = l & 1;
+  uint32_t* fb_cur = par ? p.fb[1] : p.fb[0];
+  uint32_t* fb_next = par ? p.fb[0] : p.fb[1];
+  long long t_level = 0;
+  if (leader) {
+    t_level = global_ns();
+    acc[0] += n_l;
+    acc[1] += e_l;
+    record_level(p, l, n_l, e_l, P, 1);
+  }
+  if (!ld_relaxed(&p.st->ctrl[par].fb)) {
+    build_frontier_bits(p, l, fb_cur, gw, P);
+    if (!grid_sync(p, ++*bar)) return false;
+  }
+  const int wpw = (p.nwords + P - 1) / P;
+  const long long base = (long long)gw * wpw * kWarp;
+  int work = 0;
+  const int cnt = bottom_up_chunk(p, l, fb_cur, fb_next, gw, P, p.cand + base, &work);
+  if (!grid_sync(p, ++*bar)) return false;
+  if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
+  if (p.hub_n > 0) build_hub_bits(p, gw, P);
+  compact_cta<W>(p, l, par, P, p.cand + base, p.cand_aux + base, cnt, (int)blockIdx.x, work);
+  if (!grid_sync(p, ++*bar)) return false;
+  if (leader) {
+    acc[2] += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+    acc[3] += ld_relaxed(&p.st->ctrl[par ^ 1].w);
     if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
   }
   return true;
@@ -118,12 +164,13 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_level_loop(Param
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) p.cta_smid[blockIdx.x] = sm_id();
   int bar = 0, l = 0;
-  long long acc[3] = {0, 0, 0};  // reached, edges, candidates (leader)
+  long long acc[4] = {0, 0, 0, 0};  // reached, edges, candidates, work (leader)
   bool streak = false;           // CTA 0 is running small levels alone
   while (true) {
     const int n_l = ld_relaxed(&p.st->ctrl[l & 1].n);
     const int e_l = ld_relaxed(&p.st->ctrl[l & 1].e);
-    const bool small = n_l > 0 && p.small_edges > 0 && e_l <= p.small_edges;
+    const bool bottom_up = ld_relaxed(&p.st->ctrl[l & 1].dir) != 0;
+    const bool small = n_l > 0 && p.small_edges > 0 && e_l <= p.small_edges && !bottom_up;
     if (streak && !small) {
       // CTA 0 ends its streak: the whole grid resumes at level l (or stops)
       streak = false;
@@ -151,6 +198,11 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_level_loop(Param
       }
       continue;
     }
+    if (bottom_up) {
+      if (!bu_level<W>(p, l, n_l, e_l, &bar, acc)) break;
+      ++l;
+      continue;
+    }
     streak = small;
     if (!one_level<W>(p, l, n_l, e_l, &bar, s_hub, acc, !small)) {
       if (streak) {
@@ -168,6 +220,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_level_loop(Param
     p.st->reached = acc[0];
     p.st->edges = acc[1];
     p.st->cands = acc[2];
+    p.st->work = acc[3];
   }
 }
 
@@ -196,8 +249,9 @@ __global__ void __launch_bounds__(W * kWarp) k_compact(Params p, int l, int e_l,
   }
   // every thread of the CTA takes part; warps without a chunk bring 0
   const int e_begin = gw < P_l ? (int)min((long long)gw * C_l, (long long)e_l) : 0;
+  const int e_end = gw < P_l ? (int)min((long long)gw * C_l + C_l, (long long)e_l) : 0;
   const int cnt = gw < P_l ? ld_relaxed(&p.cand_cnt[gw]) : 0;
-  compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, (int)blockIdx.x);
+  compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, (int)blockIdx.x, e_end - e_begin);
 }
 
 // CSR sanity checks that every traversal relies on (no out-of-range access):
@@ -298,7 +352,15 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     g->batch_bitmask = opts->batch_bitmask;
     if (opts->small_level_edges > 0) g->small_edges = opts->small_level_edges;
     if (opts->small_level_edges < 0) g->small_edges = 0;  // never
+    if (opts->direction != 0 && opts->direction != 1)
+      return fail(BFS_E_INVAL, "direction = %d: use 0 or 1", opts->direction);
+    g->direction = opts->direction;
+    if (opts->do_alpha < 0 || opts->do_beta < 0) return fail(BFS_E_INVAL, "do_alpha / do_beta must be >= 0");
+    if (opts->do_alpha > 0) g->alpha = opts->do_alpha;
+    if (opts->do_beta > 0) g->beta = opts->do_beta;
   }
+  if (g->direction && !(flags & BFS_SYMMETRIC))
+    return fail(BFS_E_INVAL, "direction-optimising levels need a symmetric graph (BFS_SYMMETRIC)");
   g->symmetric = (flags & BFS_SYMMETRIC) != 0;
   if (!coop) g->persistent = 0;
 
@@ -370,7 +432,7 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
         for (int32_t e = 0; e < nnz; ++e)
           if (ci[e] < 0 || ci[e] >= n) return fail(BFS_E_INVAL, "col_idx[%d] = %d out of range", e, ci[e]);
         std::vector<int32_t> perm, rp2, ci2;
-        if (s3bfs_host_relabel(n, rp, ci, &perm, &g->h_inv, &rp2, &ci2) != 0)
+        if (s3bfs_host_relabel(n, rp, ci, g->direction != 0, &perm, &g->h_inv, &rp2, &ci2) != 0)
           return fail(BFS_E_NOMEM, "renumbering: host allocation failed");
         h_rp.swap(rp2);
         h_ci.swap(ci2);
@@ -431,8 +493,18 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     if ((rc = dalloc(g, &g->d_RS[b], (size_t)n + 4)) != BFS_OK) return rc;
     if ((rc = dalloc(g, &g->d_EX[b], (size_t)n + 4)) != BFS_OK) return rc;
   }
-  if ((rc = dalloc(g, &g->d_cand, (size_t)nnz + 32)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_cand_aux, (size_t)nnz + 32)) != BFS_OK) return rc;
+  // candidates: one slot per edge of a top-down level; a bottom-up level
+  // gives each warp room for 32 vertices per bitmap word it owns
+  size_t cand_cap = (size_t)nnz + 32;
+  if (g->direction) {
+    g->nwords = (int32_t)(((long long)n + 127) / 128 * 4);
+    const size_t wpw = ((size_t)g->nwords + g->warps - 1) / g->warps;
+    cand_cap = std::max(cand_cap, wpw * 32 * (size_t)g->warps + 32);
+    for (int b = 0; b < 2; ++b)
+      if ((rc = dalloc(g, &g->d_fb[b], (size_t)g->nwords)) != BFS_OK) return rc;
+  }
+  if ((rc = dalloc(g, &g->d_cand, cand_cap)) != BFS_OK) return rc;
+  if ((rc = dalloc(g, &g->d_cand_aux, cand_cap)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_cand_cnt, (size_t)max_chunks)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_status, (size_t)max_chunks)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_arrive, (size_t)(g->ctas + 3) / 4 * 4)) != BFS_OK) return rc;
@@ -520,6 +592,12 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.hub_bits = g->d_hub_bits;
   p.hub_n = g->persistent ? g->hub_n : 0;
   p.small_edges = g->persistent ? g->small_edges : 0;
+  p.fb[0] = g->d_fb[0];
+  p.fb[1] = g->d_fb[1];
+  p.nwords = g->nwords;
+  p.direction = g->persistent ? g->direction : 0;
+  p.alpha = g->alpha;
+  p.beta = g->beta;
   return p;
 }
 
@@ -529,12 +607,14 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
   const int igrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n / 4 + 255) / 256)));
   k_init<<<igrid, kThreads, 0, g->stream>>>(p, g->ctas);
   CUDA_TRY(cudaGetLastError());
+  ++g->launches;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
   if (g->persistent) {
     Params pc = p;
     void* args[] = {&pc};
     CUDA_TRY(cudaLaunchCooperativeKernel(level_loop_fn(g->wpc), dim3(g->ctas), dim3(g->wpc * kWarp), args,
                                          loop_smem(p.hub_n), g->stream));
+    ++g->launches;
   } else {
     // launch per phase; the host reads n and e of every level
     LevelCtrl* hc = reinterpret_cast<LevelCtrl*>(g->h_ctrl);
@@ -559,6 +639,7 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
         k_compact<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
       }
       CUDA_TRY(cudaGetLastError());
+      g->launches += 2;
       CUDA_TRY(cudaMemcpyAsync(hc, &g->d_st->ctrl[(l + 1) & 1], sizeof(LevelCtrl), cudaMemcpyDeviceToHost,
                                g->stream));
       CUDA_TRY(cudaMemcpyAsync(hc + 1, &g->d_st->err, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
@@ -573,11 +654,13 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
     tail.reached = reached;
     tail.edges = edges;
     tail.cands = cands;
+    tail.work = edges;
     // num_levels and totals go to the device block so both modes read back alike
     CUDA_TRY(cudaMemcpyAsync(&g->d_st->num_levels, &tail.num_levels, sizeof(int32_t), cudaMemcpyHostToDevice,
                              g->stream));
     CUDA_TRY(cudaMemcpyAsync(&g->d_st->reached, &tail.reached, 3 * sizeof(long long), cudaMemcpyHostToDevice,
                              g->stream));
+    CUDA_TRY(cudaMemcpyAsync(&g->d_st->work, &tail.work, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
     CUDA_TRY(cudaStreamSynchronize(g->stream));
   }
   CUDA_TRY(cudaGetLastError());
@@ -606,7 +689,8 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
   stats->candidates = st.cands;
   stats->ms_level_step = 0.f;
   stats->ms_total = 0.f;
-  stats->work_edges = st.edges;
+  stats->work_edges = st.work;
+  stats->launches = g->launches;
   if (timed) {
     CUDA_TRY(cudaEventElapsedTime(&stats->ms_level_step, g->ev[1], g->ev[2]));
     CUDA_TRY(cudaEventElapsedTime(&stats->ms_total, g->ev[0], g->ev[2]));
@@ -648,6 +732,7 @@ static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* paren
   int32_t* parent = (par_dev && !g->relabel) ? parent_out : g->d_parent;
   const Params p = make_params(g, g->relabel ? g->h_inv[src] : src, level, parent);
   const bool timed = stats != nullptr;
+  g->launches = 0;
   int rc = enqueue_traversal(g, p, timed);
   if (rc != BFS_OK) return rc;
   const int32_t* lvl_src = level;
@@ -658,6 +743,7 @@ static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* paren
     const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
     k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, level, parent, lo, po);
     CUDA_TRY(cudaGetLastError());
+    ++g->launches;
     lvl_src = lo;
     par_src = po;
   }
@@ -793,13 +879,16 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
   CUDA_TRY(cudaGetLastError());
   k_msbfs_sources<<<1, 64, 0, g->stream>>>(p, g->d_groups, g->d_masks, groups, g->d_groups + 64, g->d_groups + 128);
   CUDA_TRY(cudaGetLastError());
+  g->launches = 2;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
   void* args[] = {&p};
   CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_msbfs, dim3(g->ms_ctas), dim3(kThreads), args, 0, g->stream));
+  ++g->launches;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
   if (stats) {
     k_msbfs_counts<<<g->ms_ctas, kThreads, 0, g->stream>>>(p, g->d_counts);
     CUDA_TRY(cudaGetLastError());
+    ++g->launches;
   }
   if (!lvl_dev)
     CUDA_TRY(cudaMemcpyAsync(levels_out, L, sizeof(int32_t) * (size_t)k * n, cudaMemcpyDeviceToHost, g->stream));
@@ -841,6 +930,7 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
     st.ms_level_step = ms_loop;
     st.ms_total = ms_all;
     st.work_edges = work;
+    st.launches = g->launches;
   }
   return BFS_OK;
 }

@@ -83,12 +83,20 @@ constexpr unsigned kEpochMask = 0x3FFFFFFFu;
 // written before the word is released.
 struct alignas(32) ChunkStatus {
   unsigned long long word;
-  int32_t agg_deg, agg_cand, incl_deg, incl_cand;
-  int32_t pad[2];
+  int32_t agg_deg, agg_cand, agg_work;
+  int32_t pad[3];
 };
 
+// Sizes of the frontier of one level, published by the compaction of the
+// level before (by parity of the level).
 struct LevelCtrl {
-  int32_t n, e, c, pad;
+  int32_t n, e;  // frontier size n_l and its edge count e_l
+  int32_t c;     // candidates the level before emitted
+  int32_t cum;   // e summed over this level and all earlier ones (<= nnz)
+  int32_t dir;   // how this level runs: 0 top-down, 1 bottom-up
+  int32_t fb;    // 1: the level before wrote this level's frontier bitmap
+  int32_t w;     // neighbour entries the level before examined
+  int32_t pad;
 };
 
 // Device-resident control block of one traversal.
@@ -101,6 +109,7 @@ struct DevState {
   long long reached, edges, cands;
   int32_t progress;      // levels done by CTA 0 alone (the others wait; progress extends their wait)
   int32_t resume_level;  // level at which the whole grid resumes after CTA 0 ran small levels alone
+  long long work;        // neighbour entries examined, all levels
 };
 
 struct Params {
@@ -135,6 +144,13 @@ struct Params {
   // levels with at most this many edges run on CTA 0 alone, with CTA barriers
   // instead of grid barriers (0 = never)
   int32_t small_edges;
+  // direction-optimising traversal of a symmetric graph: bottom-up levels
+  // test neighbours against the frontier bitmap fb[l & 1] (bit v set iff
+  // level[v] == l) and write the next level's bitmap fb[(l + 1) & 1]
+  uint32_t* fb[2];
+  int32_t nwords;     // words of a frontier bitmap: ceil(n / 32), padded to a multiple of 4
+  int32_t direction;  // 0: every level top-down; 1: direction-optimising
+  int32_t alpha, beta;
 };
 
 // ---------------------------------------------------------------------------
@@ -517,6 +533,20 @@ __device__ inline int explore_chunk(const Params& p, int l, int par, int n_l, in
 // COMPACT: dedup, then a single-pass look-back scan over the CTAs of a level
 // ---------------------------------------------------------------------------
 
+// Direction of the next level of a direction-optimising traversal (Beamer,
+// Asanovic and Patterson, SC 2012; the paper's conclusion names bottom-up
+// steps as compatible with S3BFS).  With m_u = nnz - cum, the degree sum of
+// the vertices still unvisited once the next frontier is known: a top-down
+// traversal turns bottom-up when the next frontier's edges exceed m_u / alpha;
+// a bottom-up one turns back when the frontier shrinks below n / beta.
+__device__ __forceinline__ int next_direction(const Params& p, int dir_l, long long n_l, long long n_next,
+                                              long long e_next, long long cum) {
+  if (!p.direction || n_next <= 0) return 0;
+  const long long m_u = (long long)p.nnz - cum;
+  if (dir_l == 0) return e_next * p.alpha > m_u ? 1 : 0;
+  return (n_next * p.beta < (long long)p.n && n_next < n_l) ? 0 : 1;
+}
+
 // Dedup (lines 19-23) and linearisation (lines 24-29) of the candidates of one
 // CTA's chunks, plus the degree gather and exclusive scan of the next frontier
 // (lines 12-15 of the next level).  Called by every thread of a CTA that holds
@@ -535,12 +565,14 @@ __device__ inline int explore_chunk(const Params& p, int l, int par, int n_l, in
 constexpr int kCompactR = S3BFS_CR;
 
 // b: rank of this CTA among the CTAs that hold the level's chunks (the scan
-// runs over ranks 0 .. (P_l - 1) / W).
+// runs over ranks 0 .. (P_l - 1) / W).  work: neighbour entries this warp
+// examined in the level (summed into the next level's control block).
 template <int W>  // warps per CTA
-__device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt, int b) {
-  __shared__ int sK[W], sD[W], sC[W];
-  __shared__ int sRed[3][W];
-  __shared__ int sPre[3];
+__device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt, int b,
+                            int work) {
+  __shared__ int sK[W], sD[W], sC[W], sW[W];
+  __shared__ int sRed[4][W];
+  __shared__ int sPre[4];
   const int lane = threadIdx.x & (kWarp - 1);
   const int wib = threadIdx.x >> 5;
   const int np = par ^ 1;
@@ -597,6 +629,7 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
     sK[wib] = K;
     sD[wib] = D;
     sC[wib] = cnt;
+    sW[wib] = work;
   }
   __syncthreads();
 
@@ -604,18 +637,20 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
   ChunkStatus* S = p.status;
   const unsigned long long ep = (unsigned long long)((unsigned)(l + 1) & kEpochMask) << 32;
   if (threadIdx.x == 0) {
-    int Kc = 0, Dc = 0, Cc = 0;
+    int Kc = 0, Dc = 0, Cc = 0, Wc = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       Kc += sK[w];
       Dc += sD[w];
       Cc += sC[w];
+      Wc += sW[w];
     }
     S[b].agg_deg = Dc;
     S[b].agg_cand = Cc;
+    S[b].agg_work = Wc;
     st_release64(&S[b].word, (kFlagAgg << 62) | ep | (unsigned)Kc);
   }
-  int kk = 0, dd = 0, cc = 0;
+  int kk = 0, dd = 0, cc = 0, ww = 0;
   bool ok = true;
   const long long t0 = global_ns();
   for (int j = threadIdx.x; j < b && ok; j += blockDim.x) {
@@ -639,29 +674,34 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
       kk += (int)(unsigned)(w & 0xffffffffull);
       dd += ld_relaxed(&S[j].agg_deg);
       cc += ld_relaxed(&S[j].agg_cand);
+      ww += ld_relaxed(&S[j].agg_work);
     }
   }
   kk = __reduce_add_sync(kFull, kk);
   dd = __reduce_add_sync(kFull, dd);
   cc = __reduce_add_sync(kFull, cc);
+  ww = __reduce_add_sync(kFull, ww);
   if (lane == 0) {
     sRed[0][wib] = kk;
     sRed[1][wib] = dd;
     sRed[2][wib] = cc;
+    sRed[3][wib] = ww;
   }
   ok = __syncthreads_and(ok);
   if (!ok) return false;
   if (threadIdx.x == 0) {
-    int a = 0, d = 0, c = 0;
+    int a = 0, d = 0, c = 0, x = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       a += sRed[0][w];
       d += sRed[1][w];
       c += sRed[2][w];
+      x += sRed[3][w];
     }
     sPre[0] = a;
     sPre[1] = d;
     sPre[2] = c;
+    sPre[3] = x;
   }
   __syncthreads();
   int Kx = sPre[0], Dx = sPre[1];
@@ -703,21 +743,32 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
     }
   }
   if (b == (P_l - 1) / W && threadIdx.x == 0) {
-    long long n_next = sPre[0], e_next = sPre[1], c_l = sPre[2];
+    long long n_next = sPre[0], e_next = sPre[1], c_l = sPre[2], w_l = sPre[3];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       n_next += sK[w];
       e_next += sD[w];
       c_l += sC[w];
+      w_l += sW[w];
     }
-    if (n_next > p.n || e_next > p.nnz || e_next < 0) {
+    const long long cum = (long long)ld_relaxed(&p.st->ctrl[par].cum) + e_next;
+    if (n_next > p.n || e_next > p.nnz || e_next < 0 || cum > p.nnz) {
       set_err(p, BFS_E_MULTIGRAPH, 4);
     } else {
       EXn[n_next] = (int)e_next;
-      st_relaxed(&p.st->ctrl[np].n, (int)n_next);
-      st_relaxed(&p.st->ctrl[np].e, (int)e_next);
-      st_relaxed(&p.st->ctrl[np].c, (int)c_l);
-      if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 2] = (int)c_l;
+      const int dir_l = ld_relaxed(&p.st->ctrl[par].dir);
+      LevelCtrl* c = &p.st->ctrl[np];
+      st_relaxed(&c->n, (int)n_next);
+      st_relaxed(&c->e, (int)e_next);
+      st_relaxed(&c->c, (int)c_l);
+      st_relaxed(&c->cum, (int)cum);
+      st_relaxed(&c->dir, next_direction(p, dir_l, ld_relaxed(&p.st->ctrl[par].n), n_next, e_next, cum));
+      st_relaxed(&c->fb, dir_l);
+      st_relaxed(&c->w, (int)w_l);
+      if (l < p.lvl_cap) {
+        p.lvl[(long long)l * kLevelFields + 2] = (int)c_l;
+        p.lvl[(long long)l * kLevelFields + 8] = (int)w_l;
+      }
     }
   }
   return true;
@@ -745,14 +796,135 @@ __device__ __forceinline__ int load_hub_bits(const Params& p, uint32_t* s_hub) {
   return p.hub_n;
 }
 
+// ---------------------------------------------------------------------------
+// BOTTOM-UP levels of a direction-optimising traversal (symmetric graphs)
+// ---------------------------------------------------------------------------
+
+// A vertex of higher degree is scanned by the whole warp, 32 entries a step.
+constexpr int kBuLight = 32;
+
+// frontier-bitmap word: written before the last grid barrier (acquire), read
+// through L1
+__device__ __forceinline__ unsigned ld_bits(const uint32_t* p) {
+  unsigned v;
+  asm volatile("ld.global.ca.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ bool in_frontier(const uint32_t* fb, int u) {
+  return (ld_bits(fb + (u >> 5)) >> (u & 31)) & 1u;
+}
+
+// Frontier bitmap of level l from the level array, after a top-down level:
+// bit v set iff level[v] == l.  One warp per 32-vertex word, ballots.
+__device__ __forceinline__ void build_frontier_bits(const Params& p, int l, uint32_t* fb, int gw, int P) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  for (int w = gw; w < p.nwords; w += P) {
+    const int v = (w << 5) + lane;
+    const int lv = v < p.n ? ld_relaxed_nb(p.level + v) : -1;
+    const unsigned m = __ballot_sync(kFull, lv == l);
+    if (lane == 0) fb[w] = m;
+  }
+}
+
+// One warp's share of a bottom-up level l: the 32-vertex words gw, gw + P,
+// ...  Every unvisited vertex v (one per lane) looks through its row, in CSR
+// order, for a neighbour in the frontier (bit set in fb_cur); the first one
+// found becomes parent[v] and v joins level l + 1.  Only v's own lane writes
+// level[v] and parent[v], so the candidates (v, parent) emitted here all
+// survive the compaction's dedup.  Writes every word of the next frontier
+// bitmap it owns (ballots).  Rows of at most kBuLight entries are walked by
+// their lane, four entries a step; longer rows by the whole warp in turn.
+// Returns the candidates written to out (at most 32 per word); *work = the
+// neighbour entries examined (warp total).
+__device__ inline int bottom_up_chunk(const Params& p, int l, const uint32_t* fb_cur, uint32_t* fb_next, int gw,
+                                      int P, int2* out, int* work) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int lnext = l + 1;
+  int cnt = 0, wk = 0;
+  for (int w = gw; w < p.nwords; w += P) {
+    const int v = (w << 5) + lane;
+    const int lv = v < p.n ? ld_relaxed_nb(p.level + v) : 0;
+    const bool unv = lv < 0;
+    int k = 0, re = 0;
+    if (unv) {
+      k = __ldg(p.row_ptr + v);
+      re = __ldg(p.row_ptr + v + 1);
+    }
+    const bool heavy = unv && re - k > kBuLight;
+    bool found = false;
+    int pu = 0;
+    bool go = unv && !heavy && k < re;
+    while (__any_sync(kFull, go)) {
+      if (go) {
+        int c[4];
+        bool h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = k + j < re ? __ldg(p.col_idx + k + j) : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = c[j] >= 0 && in_frontier(fb_cur, c[j]);
+        int taken = min(4, re - k);
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+          if (h[j]) {
+            found = true;
+            pu = c[j];
+            taken = j + 1;
+          }
+        wk += taken;
+        k += 4;
+        go = !found && k < re;
+      }
+    }
+    unsigned hm = __ballot_sync(kFull, heavy);
+    while (hm) {
+      const int j = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int hb = __shfl_sync(kFull, k, j), he = __shfl_sync(kFull, re, j);
+      int hit = -1, seen = 0;
+      for (int base = hb; base < he; base += kWarp) {
+        const int e = base + lane;
+        const int c = e < he ? __ldg(p.col_idx + e) : -1;
+        const unsigned m = __ballot_sync(kFull, c >= 0 && in_frontier(fb_cur, c));
+        if (m) {
+          const int f = __ffs(m) - 1;
+          hit = __shfl_sync(kFull, c, f);
+          seen += f + 1;
+          break;
+        }
+        seen += min(kWarp, he - base);
+      }
+      if (lane == j) {
+        wk += seen;
+        if (hit >= 0) {
+          found = true;
+          pu = hit;
+        }
+      }
+    }
+    if (found) {
+      p.level[v] = lnext;
+      p.parent[v] = pu;
+    }
+    const unsigned fm = __ballot_sync(kFull, found);
+    if (lane == 0) fb_next[w] = fm;
+    if (found) out[cnt + __popc(fm & ((1u << lane) - 1u))] = make_int2(v, pu);
+    cnt += __popc(fm);
+  }
+  *work = __reduce_add_sync(kFull, wk);
+  return cnt;
+}
+
 __device__ __forceinline__ void publish_empty_next(const Params& p, int par) {
   LevelCtrl* c = &p.st->ctrl[par ^ 1];
   st_relaxed(&c->n, 0);
   st_relaxed(&c->e, 0);
   st_relaxed(&c->c, 0);
+  st_relaxed(&c->dir, 0);
+  st_relaxed(&c->fb, 0);
+  st_relaxed(&c->w, 0);
 }
 
-__device__ __forceinline__ void record_level(const Params& p, int l, int n_l, int e_l, int P_l) {
+__device__ __forceinline__ void record_level(const Params& p, int l, int n_l, int e_l, int P_l, int dir = 0) {
   if (l < p.lvl_cap) {
     int* r = p.lvl + (long long)l * kLevelFields;
     r[0] = n_l;
@@ -762,6 +934,8 @@ __device__ __forceinline__ void record_level(const Params& p, int l, int n_l, in
     r[4] = 0;
     r[5] = 0;
     r[6] = 0;
+    r[7] = dir;
+    r[8] = 0;
   }
 }
 
@@ -810,12 +984,10 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
     p.EX[0][0] = 0;
     p.EX[0][1] = deg;
     DevState* st = p.st;
-    st->ctrl[0].n = 1;
-    st->ctrl[0].e = deg;
-    st->ctrl[0].c = 0;
-    st->ctrl[1].n = 0;
-    st->ctrl[1].e = 0;
-    st->ctrl[1].c = 0;
+    LevelCtrl c0 = {1, deg, 0, deg, 0, 0, 0, 0};
+    LevelCtrl c1 = {0, 0, 0, 0, 0, 0, 0, 0};
+    st->ctrl[0] = c0;
+    st->ctrl[1] = c1;
     st->err = 0;
     st->err_where = 0;
     st->num_levels = 0;
@@ -823,6 +995,7 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
     st->reached = st->edges = st->cands = 0;
     st->progress = 0;
     st->resume_level = 0;
+    st->work = 0;
   }
 }
 

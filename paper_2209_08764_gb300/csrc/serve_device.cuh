@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
     __syncthreads();
     if (q == -2) break;  // same decision in every CTA: they read the same slot states
     SlotDev* sd = q >= 0 ? sp.slots + q : nullptr;
-    int l = 0, par = 0, n_l = 0, e_l = 0, P_l = 0, C_l = 0, cnt = 0, e_begin = 0;
+    int l = 0, par = 0, n_l = 0, e_l = 0, P_l = 0, C_l = 0, cnt = 0, e_begin = 0, work = 0;
     if (sd) {
       const Params& p = sd->p;
       l = ld_relaxed(&sd->level);
@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
         const long long eb = (long long)gw * C_l;
         e_begin = (int)min(eb, (long long)e_l);
         const int e_end = (int)min(eb + C_l, (long long)e_l);
+        work = e_end - e_begin;
         if (e_begin < e_end)
           cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
       }
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
       if (P_l == 0) {
         if (rank == 0 && threadIdx.x == 0) publish_empty_next(p, par);
       } else if (rank * W < P_l) {
-        compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, rank);
+        compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, rank, work);
       }
       // the CTA that published the next level's sizes updates the slot
       const int last = P_l == 0 ? 0 : (P_l - 1) / W;

@@ -22,6 +22,10 @@ class Dev:
         sl = opts.get("small_level_edges", 0)
         self._small_opt = sl
         self.persistent = opts.get("persistent", 0) >= 0
+        # direction-optimising levels (persistent loop only)
+        self.direction = opts.get("direction", 0) if self.persistent else 0
+        self.alpha = opts.get("do_alpha", 0) or 15
+        self.beta = opts.get("do_beta", 0) or 18
         self.torch = torch
         self.rp = np.ascontiguousarray(rp, np.int32)
         self.ci = np.ascontiguousarray(ci, np.int32)
@@ -56,6 +60,27 @@ class Dev:
         self.g = None
 
 
+def expected_directions(n, nnz, n_l, e_l, direction, alpha, beta):
+    """Direction of every level (0 top-down, 1 bottom-up) by the switching
+    rule of a direction-optimising traversal (Beamer et al., SC 2012), from
+    the oracle's level profile: with m_u = nnz - (e summed over the levels up
+    to the next one), turn bottom-up when the next frontier's edges exceed
+    m_u / alpha; turn back when it shrinks below n / beta."""
+    d = [0]
+    cum = int(e_l[0])
+    for l in range(len(n_l) - 1):
+        n_next, e_next = int(n_l[l + 1]), int(e_l[l + 1])
+        cum += e_next
+        if not direction or n_next <= 0:
+            nd = 0
+        elif d[-1] == 0:
+            nd = 1 if e_next * alpha > nnz - cum else 0
+        else:
+            nd = 0 if (n_next * beta < n and n_next < int(n_l[l])) else 1
+        d.append(nd)
+    return np.array(d, np.int64)
+
+
 def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=64):
     """Levels bit-exact, parents a valid BFS tree, per-level statistics
     consistent with the oracle's level profile."""
@@ -70,21 +95,38 @@ def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=64
     assert st.num_levels == len(n_l)
     assert st.reached == int(n_l.sum())
     assert st.edges_scanned == int(e_l.sum())
+    dirs = expected_directions(dev.n, len(dev.ci), n_l, e_l, dev.direction, dev.alpha, dev.beta)
+    bu = dirs == 1
+    if not bu.any():
+        assert st.work_edges == st.edges_scanned
     if per_level and pl is not None:
         L = min(len(n_l), cap)
         assert np.array_equal(pl[:L, 0], n_l[:L]), "per-level n_l"
         assert np.array_equal(pl[:L, 1], e_l[:L]), "per-level e_l"
+        assert np.array_equal(pl[:L, 7], dirs[:L]), "per-level direction"
+        # work: e_l top-down; bottom-up at least one entry per vertex found
+        # and at most the degree sum of the unvisited vertices
+        td = ~bu[:L]
+        assert np.array_equal(pl[:L, 8][td], e_l[:L][td]), "top-down work != e_l"
+        nxt_all = np.append(n_l[1:], 0)
+        unvisited_deg = len(dev.ci) - np.cumsum(e_l)
+        assert np.all(pl[:L, 8][~td] >= nxt_all[:L][~td]), "bottom-up work below the vertices found"
+        assert np.all(pl[:L, 8][~td] <= unvisited_deg[:L][~td]), "bottom-up work above the unvisited degree sum"
+        assert st.work_edges == int(pl[:L, 8].sum()) or L < len(n_l)
         # candidates: at least the vertices found, at most the edges into the next level
         nxt = np.append(n_l[1:], 0)[:L]
         rows = np.repeat(np.arange(dev.n), np.diff(dev.rp))
         into = (want[rows] >= 0) & (want[dev.ci] == want[rows] + 1)
         e_next = np.bincount(want[rows][into], minlength=len(n_l))[:L]
         assert np.all(pl[:L, 2] >= nxt) and np.all(pl[:L, 2] <= e_next), "candidates out of bounds"
+        # a bottom-up level finds every new vertex exactly once
+        assert np.array_equal(pl[:L, 2][bu[:L]], nxt[bu[:L]]), "bottom-up candidates != next frontier"
         assert st.candidates == int(pl[:, 2].sum()) or L < len(n_l)
         P = dev.info["warps"]
         W = P // dev.info["ctas"]
-        small = (e_l[:L] <= dev.small) & dev.persistent
+        small = (e_l[:L] <= dev.small) & dev.persistent & ~bu[:L]
         want_P = np.where(e_l[:L] > 0, np.minimum(np.where(small, W, P), -(-e_l[:L] // grain)), 0)
+        want_P = np.where(bu[:L], P, want_P)
         if "wi" not in dev.__dict__:
             assert np.array_equal(pl[:L, 3], want_P), "active warps != min(P, ceil(e_l/grain))"
     return lv, par, st, pl

@@ -50,16 +50,47 @@ def test_host_only_calls(lib):
     lib.bfs_destroy(None)
 
 
-def test_struct_layout_matches_header():
-    # int32 x 10
-    assert ctypes.sizeof(B.bfs_opts) == 40
-    # 2 int32, 3 int64, 2 float, pointer, int32 (+ padding), int64
-    assert B.bfs_stats.per_level.offset == 40
-    assert B.bfs_stats.work_edges.offset == 56
-    assert ctypes.sizeof(B.bfs_stats) == 64
+_STRUCTS = ("bfs_opts", "bfs_stats", "bfs_server_opts", "bfs_completion")
 
 
-def test_server_struct_layout():
-    assert ctypes.sizeof(B.bfs_server_opts) == 32
-    assert B.bfs_completion.t_submit_us.offset == 40
-    assert ctypes.sizeof(B.bfs_completion) == 64
+def _c_layout(tmp_path):
+    """sizeof and offsetof of every field, as the C compiler lays the header's
+    structs out (gcc, host ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "s3bfs.h"', "int main(void) {"]
+    for st in _STRUCTS:
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for name, _ in getattr(B, st)._fields_:
+            lines.append(f'  printf("{st} {name} %zu\\n", offsetof({st}, {name}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True)
+    return {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+
+
+def test_struct_layout_matches_header(tmp_path):
+    c = _c_layout(tmp_path)
+    for st in _STRUCTS:
+        py = getattr(B, st)
+        assert c[(st, "size")] == ctypes.sizeof(py), st
+        for name, _ in py._fields_:
+            assert c[(st, name)] == getattr(py, name).offset, (st, name)
+    # the header's field lists and the binding's agree in full
+    hdr = open(os.path.join(ROOT, "include", "s3bfs.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    for st in _STRUCTS:
+        body = re.search(r"typedef struct " + st + r"\s*\{(.*?)\}\s*" + st + ";", hdr, re.S).group(1)
+        names = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:
+                first, *rest = decl.split(",")
+                names += [first.split()[-1].lstrip("*")] + [r.strip().lstrip("*") for r in rest]
+        assert names == [n for n, _ in getattr(B, st)._fields_], st
