@@ -325,8 +325,25 @@ def run_serve_mode(args, B, torch):
         service[i] = time.perf_counter() - t0
         teps[i] = st.edges_scanned // 2
     capacity = 1.0 / service.mean()                       # queries per second, one at a time
-    lam = args.serve_load * capacity
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=N))
+    loads = [float(x) for x in str(args.serve_load).split(",")]
+    base_gaps = rng.exponential(1.0, size=N)              # one Poisson stream, rescaled per load
+    for load in loads:
+        serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, capacity, load, base_gaps, t_gen)
+    for h in handles:
+        B.bfs_destroy(h)
+
+
+def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, capacity, load, base_gaps, t_gen):
+    """One arrival stream at load x the one-at-a-time capacity: the server in
+    real time, and first-come-first-served bfs_run from the measured service
+    times."""
+    N = len(gsel)
+    if load > 0:
+        lam = load * capacity
+        arrivals = np.cumsum(base_gaps / lam)
+    else:                                                 # load 0: every query at t = 0 (saturation)
+        lam = float("inf")
+        arrivals = np.zeros(N)
     # FCFS one at a time, from the measured service times
     done_fcfs = np.empty(N)
     t = 0.0
@@ -366,7 +383,8 @@ def run_serve_mode(args, B, torch):
             "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serving-pool32", "graphs": [g[0] for g in graphs], "queries": N,
-                       "load": args.serve_load, "lambda_qps": lam, "slots": args.serve_slots,
+                       "load": load if load > 0 else "all at t=0", "lambda_qps": lam if load > 0 else None,
+                       "slots": args.serve_slots,
                        "arrivals": "Poisson, graph uniform over the pool, source uniform over non-isolated, seed 5"},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "mean": float(lat.mean() * 1e3)},
@@ -374,11 +392,10 @@ def run_serve_mode(args, B, torch):
                                    "p50_ms": float(np.percentile(lat_fcfs, 50) * 1e3),
                                    "p99_ms": float(np.percentile(lat_fcfs, 99) * 1e3),
                                    "capacity_qps": capacity},
+            "throughput_qps": N / makespan,
             "failed": int(status_bad), "pool_build_s": round(t_gen, 1),
             "median_submit_delay_ms": clock_skew * 1e3}
     print(json.dumps(line), flush=True)
-    for h in handles:
-        B.bfs_destroy(h)
 
 
 def main():
@@ -405,6 +422,9 @@ def main():
     ap.add_argument("--levels", action="store_true", help="add the per-level statistics of the first source")
     ap.add_argument("--direction", type=int, default=0,
                     help="1: direction-optimising traversal (bottom-up levels) as the measured line")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose the options by the autotuner (coordinate descent on 4 of the sources)")
+    ap.add_argument("--tune-cache", default="", help="JSON cache file of the autotuner")
     ap.add_argument("--with-do", type=int, default=1,
                     help="1 (default): add a direction-optimising run of the same sources to the top-down line")
     ap.add_argument("--batch", action="store_true",
@@ -413,8 +433,9 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="query server over the 32-graph pool: Poisson stream, p50/p99 latency")
     ap.add_argument("--serve-queries", type=int, default=2000)
-    ap.add_argument("--serve-load", type=float, default=0.7,
-                    help="arrival rate as a fraction of the one-at-a-time capacity")
+    ap.add_argument("--serve-load", default="0.7",
+                    help="arrival rates as fractions of the one-at-a-time capacity, comma-separated; "
+                         "0 = every query at t = 0 (saturation throughput)")
     ap.add_argument("--serve-slots", type=int, default=64)
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
@@ -448,8 +469,20 @@ def main():
     if args.batch:
         run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas)
         return
-    line = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, args.direction)
-    if rank == 0 and not args.direction and args.with_do and w["kind"] != "grid":
+    tuned, tune_info = None, None
+    if args.autotune:
+        from paper_2209_08764_gb300 import autotune
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        t0 = time.perf_counter()
+        opts, key, info = autotune.tune(B, rp, ci, srcs[:4], cache_path=args.tune_cache or None,
+                                        symmetric=True, flags=B.BFS_VALIDATE)
+        tuned = autotune.resolve(opts, sms)
+        tune_info = {"class": key, "chosen": opts, "tuning_s": round(time.perf_counter() - t0, 1), **info}
+    direction = int(tuned.get("direction", 0)) if tuned else args.direction
+    line = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, direction, tuned=tuned)
+    if rank == 0 and tune_info:
+        line["autotune"] = tune_info
+    if rank == 0 and not direction and args.with_do and w["kind"] != "grid":
         # the same sources with direction-optimising levels (bottom-up where the
         # frontier is large); the headline value stays the top-down level step
         do = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, 1, summary=True)
@@ -488,7 +521,8 @@ def level_bytes(n, rows):
     return total
 
 
-def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, direction, summary=False):
+def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, direction, summary=False,
+                   tuned=None):
     """Single-source traversals of every source, K timed steps: the bench line
     (or, with summary, its compact form for the direction-optimising run)."""
     n, nnz = len(rp) - 1, len(ci)
@@ -503,6 +537,8 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     opts.small_level_edges = args.small_level_edges
     opts.cta_warps = args.cta_warps
     opts.direction = direction
+    for k, v in (tuned or {}).items():
+        setattr(opts, k, int(v))
     # top-down: the CSR is checked on the host (BFS_VALIDATE).  The
     # direction-optimising graph declares BFS_SYMMETRIC without that (slow)
     # host check: the generators' output is symmetric and simple, which the
@@ -622,6 +658,7 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     if rank == 0:
         config = config_of(args.workload, w, rp, ci)
         config["direction"] = "direction-optimising (alpha 15, beta 18)" if direction else "top-down (S3BFS level step)"
+        config["options"] = {f: getattr(opts, f) for f, _ in opts._fields_ if getattr(opts, f)}
         line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",

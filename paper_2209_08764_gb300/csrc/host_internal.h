@@ -34,6 +34,7 @@ struct bfs_graph {
   int alpha = 15, beta = 18;
   int32_t nwords = 0;    // words of a frontier bitmap
   uint32_t* d_fb[2] = {nullptr, nullptr};
+  int32_t *d_ulist = nullptr, *d_ulist_cnt = nullptr;  // bottom-up: unvisited vertices per warp
   int32_t lvl_cap = 0;
   int hub_n = 0;         // vertices [0, hub_n) have visited bits in shared memory
   bool relabel = false;  // internal ids are degree-descending (hubs first)

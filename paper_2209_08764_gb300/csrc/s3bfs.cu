@@ -113,13 +113,14 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
 }
 
 // One bottom-up level on the whole grid (direction-optimising traversal of a
-// symmetric graph).  If the level before ran top-down, the frontier bitmap
-// is first built from the level array (grid barrier).  Every warp then scans
-// its share of the unvisited vertices for a parent in the frontier (grid
-// barrier), and the standard compaction turns the new vertices into the next
-// frontier record and publishes its sizes (grid barrier).  Warp gw's
-// candidates go to its own region of the candidate buffer, room for 32
-// vertices per word it owns.
+// symmetric graph).  After a top-down level the frontier bitmap is first
+// built from the level array (grid barrier) and every vertex word is
+// scanned; after a bottom-up level only the warps' unvisited lists are.
+// Then (grid barrier) the next level's frontier bitmap is built from the
+// level array while the standard compaction turns the new vertices into the
+// next frontier record and publishes its sizes (grid barrier).  Warp gw's
+// candidates and unvisited list use its own region: room for the 128
+// vertices of every group of four bitmap words it owns.
 template <int W>
 __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, int* bar, long long* acc) {
   const int gw = blockIdx.x * W + (threadIdx.x >> 5);
@@ -135,16 +136,20 @@ __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, 
     acc[1] += e_l;
     record_level(p, l, n_l, e_l, P, 1);
   }
-  if (!ld_relaxed(&p.st->ctrl[par].fb)) {
+  const bool after_bu = ld_relaxed(&p.st->ctrl[par].fb) != 0;
+  if (!after_bu) {
     build_frontier_bits(p, l, fb_cur, gw, P);
     if (!grid_sync(p, ++*bar)) return false;
   }
-  const int wpw = (p.nwords + P - 1) / P;
-  const long long base = (long long)gw * wpw * kWarp;
+  // warp gw's region: 128 entries per 128-vertex group it owns
+  const int gpw = ((p.nwords >> 2) + P - 1) / P;
+  const long long base = (long long)gw * gpw * 128;
   int work = 0;
-  const int cnt = bottom_up_chunk(p, l, fb_cur, fb_next, gw, P, p.cand + base, &work);
+  const int total = after_bu ? ld_relaxed(p.ulist_cnt + gw) : bu_unvisited(p, gw, P, p.ulist + base);
+  const int cnt = bu_scan(p, l, fb_cur, gw, total, p.ulist + base, p.cand + base, &work);
   if (!grid_sync(p, ++*bar)) return false;
   if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
+  build_frontier_bits(p, l + 1, fb_next, gw, P);
   if (p.hub_n > 0) build_hub_bits(p, gw, P);
   compact_cta<W>(p, l, par, P, p.cand + base, p.cand_aux + base, cnt, (int)blockIdx.x, work);
   if (!grid_sync(p, ++*bar)) return false;
@@ -494,14 +499,17 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     if ((rc = dalloc(g, &g->d_EX[b], (size_t)n + 4)) != BFS_OK) return rc;
   }
   // candidates: one slot per edge of a top-down level; a bottom-up level
-  // gives each warp room for 32 vertices per bitmap word it owns
+  // gives each warp room for the 128 vertices of each group of four bitmap
+  // words it owns
   size_t cand_cap = (size_t)nnz + 32;
   if (g->direction) {
     g->nwords = (int32_t)(((long long)n + 127) / 128 * 4);
-    const size_t wpw = ((size_t)g->nwords + g->warps - 1) / g->warps;
-    cand_cap = std::max(cand_cap, wpw * 32 * (size_t)g->warps + 32);
+    const size_t gpw = ((size_t)g->nwords / 4 + g->warps - 1) / g->warps;
+    cand_cap = std::max(cand_cap, gpw * 128 * (size_t)g->warps + 32);
     for (int b = 0; b < 2; ++b)
       if ((rc = dalloc(g, &g->d_fb[b], (size_t)g->nwords)) != BFS_OK) return rc;
+    if ((rc = dalloc(g, &g->d_ulist, cand_cap)) != BFS_OK) return rc;
+    if ((rc = dalloc(g, &g->d_ulist_cnt, (size_t)g->warps)) != BFS_OK) return rc;
   }
   if ((rc = dalloc(g, &g->d_cand, cand_cap)) != BFS_OK) return rc;
   if ((rc = dalloc(g, &g->d_cand_aux, cand_cap)) != BFS_OK) return rc;
@@ -595,6 +603,8 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.fb[0] = g->d_fb[0];
   p.fb[1] = g->d_fb[1];
   p.nwords = g->nwords;
+  p.ulist = g->d_ulist;
+  p.ulist_cnt = g->d_ulist_cnt;
   p.direction = g->persistent ? g->direction : 0;
   p.alpha = g->alpha;
   p.beta = g->beta;

@@ -149,6 +149,10 @@ struct Params {
   // level[v] == l) and write the next level's bitmap fb[(l + 1) & 1]
   uint32_t* fb[2];
   int32_t nwords;     // words of a frontier bitmap: ceil(n / 32), padded to a multiple of 4
+  // per warp: the vertices still unvisited after a bottom-up level (in the
+  // warp's region, like its candidates) and their count
+  int32_t* ulist;
+  int32_t* ulist_cnt;
   int32_t direction;  // 0: every level top-down; 1: direction-optimising
   int32_t alpha, beta;
 };
@@ -774,16 +778,30 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
   return true;
 }
 
-// Visited bits of vertices [0, hub_n), one warp per 32-vertex word, from the
-// level array after a level's explore (all its level stores are visible).
-__device__ __forceinline__ void build_hub_bits(const Params& p, int gw, int P) {
+// Bits of vertices [0, 32 * words) from the level array: bit v set iff
+// level[v] == l, or iff level[v] >= 0 (visited) when l < 0.  A warp writes
+// four words at a time (four coalesced loads in flight per lane, one ballot
+// per word); words is a multiple of 4.  Every word is written.
+__device__ __forceinline__ void level_bits(const Params& p, int l, int words, uint32_t* out, int gw, int P) {
   const int lane = threadIdx.x & (kWarp - 1);
-  const int words = p.hub_n >> 5;
-  for (int w = gw; w < words; w += P) {
-    const int lv = ld_relaxed_nb(p.level + (w << 5) + lane);
-    const unsigned m = __ballot_sync(kFull, lv >= 0);
-    if (lane == 0) p.hub_bits[w] = m;
+  for (int q = gw; q < (words >> 2); q += P) {
+    int lv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = (q << 7) + (j << 5) + lane;
+      lv[j] = v < p.n ? ld_relaxed_nb(p.level + v) : -1;
+    }
+    unsigned m[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m[j] = __ballot_sync(kFull, l >= 0 ? lv[j] == l : lv[j] >= 0);
+    if (lane < 4) out[(q << 2) + lane] = lane == 0 ? m[0] : lane == 1 ? m[1] : lane == 2 ? m[2] : m[3];
   }
+}
+
+// Visited bits of vertices [0, hub_n), from the level array after a level's
+// explore (all its level stores are visible).
+__device__ __forceinline__ void build_hub_bits(const Params& p, int gw, int P) {
+  level_bits(p, -1, p.hub_n >> 5, p.hub_bits, gw, P);
 }
 
 // Copies the visited bits into shared memory (whole CTA); returns hub_n.
@@ -800,8 +818,12 @@ __device__ __forceinline__ int load_hub_bits(const Params& p, uint32_t* s_hub) {
 // BOTTOM-UP levels of a direction-optimising traversal (symmetric graphs)
 // ---------------------------------------------------------------------------
 
-// A vertex of higher degree is scanned by the whole warp, 32 entries a step.
-constexpr int kBuLight = 32;
+// Entries of its row a lane tests by itself; a longer row without a parent in
+// them is then scanned by the whole warp, 32 entries a step.
+#ifndef S3BFS_BU_LANE
+#define S3BFS_BU_LANE 32
+#endif
+constexpr int kBuLane = S3BFS_BU_LANE;
 
 // frontier-bitmap word: written before the last grid barrier (acquire), read
 // through L1
@@ -814,102 +836,185 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* fb, int u) {
   return (ld_bits(fb + (u >> 5)) >> (u & 31)) & 1u;
 }
 
-// Frontier bitmap of level l from the level array, after a top-down level:
-// bit v set iff level[v] == l.  One warp per 32-vertex word, ballots.
+// Frontier bitmap of level l from the level array: bit v set iff level[v] == l.
 __device__ __forceinline__ void build_frontier_bits(const Params& p, int l, uint32_t* fb, int gw, int P) {
-  const int lane = threadIdx.x & (kWarp - 1);
-  for (int w = gw; w < p.nwords; w += P) {
-    const int v = (w << 5) + lane;
-    const int lv = v < p.n ? ld_relaxed_nb(p.level + v) : -1;
-    const unsigned m = __ballot_sync(kFull, lv == l);
-    if (lane == 0) fb[w] = m;
-  }
+  level_bits(p, l, p.nwords, fb, gw, P);
 }
 
-// One warp's share of a bottom-up level l: the 32-vertex words gw, gw + P,
-// ...  Every unvisited vertex v (one per lane) looks through its row, in CSR
-// order, for a neighbour in the frontier (bit set in fb_cur); the first one
-// found becomes parent[v] and v joins level l + 1.  Only v's own lane writes
-// level[v] and parent[v], so the candidates (v, parent) emitted here all
-// survive the compaction's dedup.  Writes every word of the next frontier
-// bitmap it owns (ballots).  Rows of at most kBuLight entries are walked by
-// their lane, four entries a step; longer rows by the whole warp in turn.
-// Returns the candidates written to out (at most 32 per word); *work = the
-// neighbour entries examined (warp total).
-__device__ inline int bottom_up_chunk(const Params& p, int l, const uint32_t* fb_cur, uint32_t* fb_next, int gw,
-                                      int P, int2* out, int* work) {
+// Vertices per lane in a bottom-up scan (independent parent searches in
+// flight together).
+#ifndef S3BFS_BU_V
+#define S3BFS_BU_V 2
+#endif
+constexpr int kBuV = S3BFS_BU_V;
+// entries tested in the first step of a row (1 to 4)
+#ifndef S3BFS_BU_FIRST
+#define S3BFS_BU_FIRST 1
+#endif
+constexpr int kBuFirst = S3BFS_BU_FIRST;
+
+// Parent search of kBuV unvisited vertices per lane (slot j active if act[j];
+// row entries [k[j], re[j]) in CSR order).  Each lane tests the first kBuLane
+// entries of its rows, four a step per row; the rows still without a parent
+// after that are scanned by the whole warp in turn, 32 entries a step.  The
+// first neighbour in the frontier (bit set in fb) is the parent.  Warp-wide.
+__device__ __forceinline__ void bu_search(const Params& p, const uint32_t* fb, const bool* act, int* k, const int* re,
+                                          bool* found, int* pu, int* wk) {
   const int lane = threadIdx.x & (kWarp - 1);
-  const int lnext = l + 1;
-  int cnt = 0, wk = 0;
-  for (int w = gw; w < p.nwords; w += P) {
-    const int v = (w << 5) + lane;
-    const int lv = v < p.n ? ld_relaxed_nb(p.level + v) : 0;
-    const bool unv = lv < 0;
-    int k = 0, re = 0;
-    if (unv) {
-      k = __ldg(p.row_ptr + v);
-      re = __ldg(p.row_ptr + v + 1);
-    }
-    const bool heavy = unv && re - k > kBuLight;
-    bool found = false;
-    int pu = 0;
-    bool go = unv && !heavy && k < re;
-    while (__any_sync(kFull, go)) {
-      if (go) {
-        int c[4];
-        bool h[4];
+  int lim[kBuV];
+  bool go[kBuV];
+  bool any = false;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) c[j] = k + j < re ? __ldg(p.col_idx + k + j) : -1;
+  for (int s = 0; s < kBuV; ++s) {
+    found[s] = false;
+    pu[s] = 0;
+    lim[s] = act[s] ? min(re[s], k[s] + kBuLane) : k[s];
+    go[s] = act[s] && k[s] < lim[s];
+    any |= go[s];
+  }
+  // the first step tests kBuFirst entries (the row's first entries are its
+  // highest-degree neighbours on a renumbered graph, the likeliest to be in
+  // the frontier); every later step four
+  int seen = 0, width = kBuFirst;
+  while (__any_sync(kFull, any)) {
+    int c[kBuV][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) h[j] = c[j] >= 0 && in_frontier(fb_cur, c[j]);
-        int taken = min(4, re - k);
+    for (int s = 0; s < kBuV; ++s)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        c[s][j] = go[s] && j < width && k[s] + j < lim[s] ? __ldg(p.col_idx + k[s] + j) : -1;
+    bool h[kBuV][4];
+#pragma unroll
+    for (int s = 0; s < kBuV; ++s)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) h[s][j] = c[s][j] >= 0 && in_frontier(fb, c[s][j]);
+    any = false;
+#pragma unroll
+    for (int s = 0; s < kBuV; ++s) {
+      if (go[s]) {
+        int taken = min(width, lim[s] - k[s]);
 #pragma unroll
         for (int j = 3; j >= 0; --j)
-          if (h[j]) {
-            found = true;
-            pu = c[j];
+          if (h[s][j]) {
+            found[s] = true;
+            pu[s] = c[s][j];
             taken = j + 1;
           }
-        wk += taken;
-        k += 4;
-        go = !found && k < re;
+        seen += taken;
+        k[s] = min(k[s] + width, lim[s]);  // the warp phase resumes exactly at lim
+        go[s] = !found[s] && k[s] < lim[s];
       }
+      any |= go[s];
     }
-    unsigned hm = __ballot_sync(kFull, heavy);
+    width = 4;
+  }
+#pragma unroll
+  for (int s = 0; s < kBuV; ++s) {
+    unsigned hm = __ballot_sync(kFull, act[s] && !found[s] && k[s] < re[s]);
     while (hm) {
       const int j = __ffs(hm) - 1;
       hm &= hm - 1;
-      const int hb = __shfl_sync(kFull, k, j), he = __shfl_sync(kFull, re, j);
-      int hit = -1, seen = 0;
+      const int hb = __shfl_sync(kFull, k[s], j), he = __shfl_sync(kFull, re[s], j);
+      int hit = -1, n_seen = 0;
       for (int base = hb; base < he; base += kWarp) {
         const int e = base + lane;
         const int c = e < he ? __ldg(p.col_idx + e) : -1;
-        const unsigned m = __ballot_sync(kFull, c >= 0 && in_frontier(fb_cur, c));
+        const unsigned m = __ballot_sync(kFull, c >= 0 && in_frontier(fb, c));
         if (m) {
-          const int f = __ffs(m) - 1;
-          hit = __shfl_sync(kFull, c, f);
-          seen += f + 1;
+          const int first = __ffs(m) - 1;
+          hit = __shfl_sync(kFull, c, first);
+          n_seen += first + 1;
           break;
         }
-        seen += min(kWarp, he - base);
+        n_seen += min(kWarp, he - base);
       }
       if (lane == j) {
-        wk += seen;
+        seen += n_seen;
         if (hit >= 0) {
-          found = true;
-          pu = hit;
+          found[s] = true;
+          pu[s] = hit;
         }
       }
     }
-    if (found) {
-      p.level[v] = lnext;
-      p.parent[v] = pu;
-    }
-    const unsigned fm = __ballot_sync(kFull, found);
-    if (lane == 0) fb_next[w] = fm;
-    if (found) out[cnt + __popc(fm & ((1u << lane) - 1u))] = make_int2(v, pu);
-    cnt += __popc(fm);
   }
+  *wk += seen;
+}
+
+// A bottom-up level that follows a top-down one starts by listing, per warp,
+// the unvisited vertices of degree > 0 among the 128-vertex groups gw, gw +
+// P, ... (level and row bounds of four 32-vertex words in flight per lane).
+// Returns the list length; the list goes to ulist (at most 128 per group).
+__device__ inline int bu_unvisited(const Params& p, int gw, int P, int* ulist) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const unsigned lt = (1u << lane) - 1u;
+  int cnt = 0;
+  for (int q = gw; q < (p.nwords >> 2); q += P) {
+    int lv[4], rs[4], re[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = (q << 7) + (j << 5) + lane;
+      lv[j] = v < p.n ? ld_relaxed_nb(p.level + v) : 0;
+      rs[j] = v <= p.n ? __ldg(p.row_ptr + v) : 0;  // row_ptr[n] ends the last row
+      re[j] = __shfl_down_sync(kFull, rs[j], 1);
+      if (lane == kWarp - 1) re[j] = v < p.n ? __ldg(p.row_ptr + v + 1) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = (q << 7) + (j << 5) + lane;
+      const bool keep = v < p.n && lv[j] < 0 && re[j] > rs[j];
+      const unsigned km = __ballot_sync(kFull, keep);
+      if (keep) ulist[cnt + __popc(km & lt)] = v;
+      cnt += __popc(km);
+    }
+  }
+  return cnt;
+}
+
+// One warp's share of a bottom-up level l: its list of unvisited vertices
+// (kBuV * 32 at a time).  Every vertex looks for a parent in the frontier of
+// level l; a vertex found gets level l + 1 and its parent from its own lane
+// (no other lane writes it, so the candidates (v, parent) emitted here all
+// survive the compaction's dedup); the others stay in the list, compacted in
+// place (a kept entry never lands past one not yet read).  Returns the
+// candidates written to out; *work = neighbour entries examined (warp total).
+__device__ inline int bu_scan(const Params& p, int l, const uint32_t* fb, int gw, int total, int* ulist, int2* out,
+                              int* work) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const unsigned lt = (1u << lane) - 1u;
+  int cnt = 0, kept = 0, wk = 0;
+  for (int b = 0; b < total; b += kWarp * kBuV) {
+    bool act[kBuV];
+    int v[kBuV], k[kBuV], re[kBuV];
+#pragma unroll
+    for (int s = 0; s < kBuV; ++s) {
+      const int i = b + s * kWarp + lane;
+      act[s] = i < total;
+      v[s] = act[s] ? ld_relaxed_nb(ulist + i) : 0;
+    }
+#pragma unroll
+    for (int s = 0; s < kBuV; ++s) {
+      k[s] = act[s] ? __ldg(p.row_ptr + v[s]) : 0;
+      re[s] = act[s] ? __ldg(p.row_ptr + v[s] + 1) : 0;
+    }
+    bool found[kBuV];
+    int pu[kBuV];
+    bu_search(p, fb, act, k, re, found, pu, &wk);
+#pragma unroll
+    for (int s = 0; s < kBuV; ++s) {
+      if (found[s]) {
+        p.level[v[s]] = l + 1;
+        p.parent[v[s]] = pu[s];
+      }
+      const unsigned fm = __ballot_sync(kFull, found[s]);
+      if (found[s]) out[cnt + __popc(fm & lt)] = make_int2(v[s], pu[s]);
+      cnt += __popc(fm);
+      const bool keep = act[s] && !found[s];
+      const unsigned km = __ballot_sync(kFull, keep);
+      if (keep) ulist[kept + __popc(km & lt)] = v[s];
+      kept += __popc(km);
+    }
+  }
+  if (lane == 0) p.ulist_cnt[gw] = kept;
   *work = __reduce_add_sync(kFull, wk);
   return cnt;
 }
