@@ -34,6 +34,7 @@ SPACE = {
     "ctas": [0, -1],          # -1: one CTA per SM (resolved by the caller)
     "relabel": [0, -1, 1],
     "direction": [0, 1],      # tried only on symmetric graphs
+    "do_alpha": [0, 4, 60],   # bottom-up switch threshold (0 = 15)
 }
 
 
@@ -167,6 +168,7 @@ def tune(B, rp, ci, sources, cache_path=None, symmetric=True, flags=0, space=Non
     sp = dict(SPACE if space is None else space)
     if not symmetric:
         sp.pop("direction", None)
+        sp.pop("do_alpha", None)
     best, best_ms, trials = coordinate_descent(make_measure(B, rp, ci, sources, flags, stream, sms, reps), sp)
     cache.put(key, best, best_ms, [[o, ms] for o, ms in trials])
     return best, key, {"cached": False, "ms": best_ms, "trials": len(trials)}

@@ -137,10 +137,12 @@ __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, 
     record_level(p, l, n_l, e_l, P, 1);
   }
   const bool after_bu = ld_relaxed(&p.st->ctrl[par].fb) != 0;
+#if S3BFS_BU_BITMAP
   if (!after_bu) {
     build_frontier_bits(p, l, fb_cur, gw, P);
     if (!grid_sync(p, ++*bar)) return false;
   }
+#endif
   // warp gw's region: 128 entries per 128-vertex group it owns
   const int gpw = ((p.nwords >> 2) + P - 1) / P;
   const long long base = (long long)gw * gpw * 128;
@@ -149,7 +151,11 @@ __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, 
   const int cnt = bu_scan(p, l, fb_cur, gw, total, p.ulist + base, p.cand + base, &work);
   if (!grid_sync(p, ++*bar)) return false;
   if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
+#if S3BFS_BU_BITMAP
   build_frontier_bits(p, l + 1, fb_next, gw, P);
+#else
+  (void)fb_next;
+#endif
   if (p.hub_n > 0) build_hub_bits(p, gw, P);
   compact_cta<W>(p, l, par, P, p.cand + base, p.cand_aux + base, cnt, (int)blockIdx.x, work);
   if (!grid_sync(p, ++*bar)) return false;

@@ -832,8 +832,23 @@ __device__ __forceinline__ unsigned ld_bits(const uint32_t* p) {
   asm volatile("ld.global.ca.b32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
-__device__ __forceinline__ bool in_frontier(const uint32_t* fb, int u) {
+// Is u in the frontier of level l?  With S3BFS_BU_BITMAP the test reads the
+// frontier bitmap (n bits, rebuilt from the level array around every
+// bottom-up level); without, the level array itself (level[u] == l: no
+// rebuild passes and no grid barrier for them, one 32-byte sector per test
+// instead of one per 256 vertices).
+#ifndef S3BFS_BU_BITMAP
+#define S3BFS_BU_BITMAP 0
+#endif
+__device__ __forceinline__ bool in_frontier(const Params& p, const uint32_t* fb, int l, int u) {
+#if S3BFS_BU_BITMAP
+  (void)p;
+  (void)l;
   return (ld_bits(fb + (u >> 5)) >> (u & 31)) & 1u;
+#else
+  (void)fb;
+  return ld_level(p.level + u) == l;
+#endif
 }
 
 // Frontier bitmap of level l from the level array: bit v set iff level[v] == l.
@@ -858,8 +873,8 @@ constexpr int kBuFirst = S3BFS_BU_FIRST;
 // entries of its rows, four a step per row; the rows still without a parent
 // after that are scanned by the whole warp in turn, 32 entries a step.  The
 // first neighbour in the frontier (bit set in fb) is the parent.  Warp-wide.
-__device__ __forceinline__ void bu_search(const Params& p, const uint32_t* fb, const bool* act, int* k, const int* re,
-                                          bool* found, int* pu, int* wk) {
+__device__ __forceinline__ void bu_search(const Params& p, const uint32_t* fb, int l, const bool* act, int* k,
+                                          const int* re, bool* found, int* pu, int* wk) {
   const int lane = threadIdx.x & (kWarp - 1);
   int lim[kBuV];
   bool go[kBuV];
@@ -887,7 +902,7 @@ __device__ __forceinline__ void bu_search(const Params& p, const uint32_t* fb, c
 #pragma unroll
     for (int s = 0; s < kBuV; ++s)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) h[s][j] = c[s][j] >= 0 && in_frontier(fb, c[s][j]);
+      for (int j = 0; j < 4; ++j) h[s][j] = c[s][j] >= 0 && in_frontier(p, fb, l, c[s][j]);
     any = false;
 #pragma unroll
     for (int s = 0; s < kBuV; ++s) {
@@ -919,7 +934,7 @@ __device__ __forceinline__ void bu_search(const Params& p, const uint32_t* fb, c
       for (int base = hb; base < he; base += kWarp) {
         const int e = base + lane;
         const int c = e < he ? __ldg(p.col_idx + e) : -1;
-        const unsigned m = __ballot_sync(kFull, c >= 0 && in_frontier(fb, c));
+        const unsigned m = __ballot_sync(kFull, c >= 0 && in_frontier(p, fb, l, c));
         if (m) {
           const int first = __ffs(m) - 1;
           hit = __shfl_sync(kFull, c, first);
@@ -998,7 +1013,7 @@ __device__ inline int bu_scan(const Params& p, int l, const uint32_t* fb, int gw
     }
     bool found[kBuV];
     int pu[kBuV];
-    bu_search(p, fb, act, k, re, found, pu, &wk);
+    bu_search(p, fb, l, act, k, re, found, pu, &wk);
 #pragma unroll
     for (int s = 0; s < kBuV; ++s) {
       if (found[s]) {
