@@ -75,9 +75,10 @@ typedef struct bfs_opts {
                                barrier: high-diameter graphs have thousands of tiny
                                levels.  0 = default (256 per warp of one CTA: 8192 with
                                32-warp CTAs, 2048 with 8-warp CTAs), -1 = never */
-  int32_t cta_warps;        /* warps per CTA of the level loop: 32 (one CTA per SM,
-                               one copy of the shared-memory visited bits) or 8;
-                               0 = 32 when visited bits are kept, else 8 */
+  int32_t cta_warps;        /* warps per CTA of the level loop: 8 (four CTAs per SM),
+                               or 16, 24, 32 (one CTA per SM, one copy of the
+                               shared-memory visited bits; 128, 80 or 64 registers a
+                               thread); 0 = 32 when visited bits are kept, else 8 */
   int32_t direction;        /* 0 (default): every level top-down, the S3BFS level step.
                                1: direction-optimising (needs BFS_SYMMETRIC, else
                                bfs_create_csr fails with BFS_E_INVAL): a level whose

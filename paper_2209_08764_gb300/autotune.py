@@ -1,7 +1,7 @@
 """Autotuner of the traversal options per graph class, with a JSON cache.
 
 The level step has a few knobs whose best values depend on the graph: the
-CTA shape (8 or 32 warps), the grain (minimum edges per warp chunk), the
+CTA shape (8, 16 or 32 warps), the grain (minimum edges per warp chunk), the
 small-level threshold (levels run by one CTA), the persistent grid size, the
 renumbering with shared-memory visited bits, and direction-optimising levels.
 A deep, thin graph (a mesh) spends its time in thousands of tiny levels and
@@ -28,7 +28,7 @@ import numpy as np
 # knob -> values tried (0 = the library default); the order is the order of
 # the coordinate descent
 SPACE = {
-    "cta_warps": [0, 8, 32],
+    "cta_warps": [0, 8, 16, 32],
     "small_level_edges": [0, -1, 2048, 8192, 32768],
     "chunk_edges": [0, 32, 128, 512],
     "ctas": [0, -1],          # -1: one CTA per SM (resolved by the caller)

@@ -31,11 +31,17 @@ int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, bool sor
 // dynamic shared memory of the level loop: the visited bits
 static size_t loop_smem(int hub_n) { return (size_t)hub_n / 8; }
 
-template <int W>
+template <int W, bool DO>
 __global__ void k_level_loop(Params p);
-// the level loop for a CTA shape
-static const void* level_loop_fn(int wpc) {
-  return wpc == 32 ? (const void*)k_level_loop<32> : (const void*)k_level_loop<8>;
+// the level loop for a CTA shape; DO: with bottom-up levels (a separate
+// kernel, so that the top-down loop carries no trace of them)
+static const void* level_loop_fn(int wpc, bool DO) {
+  switch (wpc) {
+    case 32: return DO ? (const void*)k_level_loop<32, true> : (const void*)k_level_loop<32, false>;
+    case 24: return DO ? (const void*)k_level_loop<24, true> : (const void*)k_level_loop<24, false>;
+    case 16: return DO ? (const void*)k_level_loop<16, true> : (const void*)k_level_loop<16, false>;
+    default: return DO ? (const void*)k_level_loop<8, true> : (const void*)k_level_loop<8, false>;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -56,9 +62,15 @@ __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) { init_tr
 // CTAs with grid barriers.  Otherwise CTA 0 alone, its warps taking the
 // chunks, with CTA barriers (small levels).  Returns false if the traversal
 // must stop (an error, including a wait that ran out).
+//
+// s_ctrl (shared memory) holds the control block of level l for CTA 0 while
+// it runs small levels alone: it reads the level's sizes from there and the
+// compaction leaves the next level's there, so a small level makes no round
+// trip to global memory for them; the global error word is then read every
+// 32 levels (an error this CTA raises itself shows in s_ctrl).
 template <int W>
 __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e_l, int* bar, uint32_t* s_hub,
-                                       long long* acc, bool GRID) {
+                                       long long* acc, bool GRID, LevelCtrl* s_ctrl) {
   __shared__ int s_err;
   const int lane = threadIdx.x & (kWarp - 1);
   const int gw = GRID ? blockIdx.x * W + (threadIdx.x >> 5) : (threadIdx.x >> 5);
@@ -92,21 +104,28 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
   if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
   if (GRID && p.hub_n > 0) build_hub_bits(p, gw, P);
   if (P_l == 0) {
-    if (gw == 0 && lane == 0) publish_empty_next(p, par);
+    if (gw == 0 && lane == 0) {
+      publish_empty_next(p, par);
+      if (!GRID) *s_ctrl = LevelCtrl{0, 0, 0, s_ctrl->cum, 0, 0, 0, 0};
+    }
   } else if (!GRID || (int)blockIdx.x * W < P_l) {
-    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0, work);
+    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0, work,
+                   GRID ? nullptr : s_ctrl);
   }
   if (GRID) {
     if (!grid_sync(p, ++*bar)) return false;
   } else {
     __syncthreads();
-    if (threadIdx.x == 0) s_err = ld_relaxed(&p.st->err);
-    __syncthreads();
-    if (s_err != 0) return false;
+    if ((l & 31) == 31) {
+      if (threadIdx.x == 0) s_err = ld_relaxed(&p.st->err);
+      __syncthreads();
+      if (s_err != 0) return false;
+    }
+    if (s_ctrl->n < 0) return false;
   }
   if (leader) {
-    acc[2] += ld_relaxed(&p.st->ctrl[par ^ 1].c);
-    acc[3] += ld_relaxed(&p.st->ctrl[par ^ 1].w);
+    acc[2] += GRID ? ld_relaxed(&p.st->ctrl[par ^ 1].c) : s_ctrl->c;
+    acc[3] += GRID ? ld_relaxed(&p.st->ctrl[par ^ 1].w) : s_ctrl->w;
     if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
   }
   return true;
@@ -167,20 +186,31 @@ __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, 
   return true;
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_level_loop(Params p) {
+// 8-warp CTAs: four per SM (64 registers a thread); wider CTAs: one per SM
+// (64, 80 or 128 registers a thread with 32, 24 or 16 warps)
+template <int W, bool DO>
+__global__ void __launch_bounds__(W * kWarp, W == 8 ? 4 : 1) k_level_loop(Params p) {
   extern __shared__ __align__(16) uint32_t s_hub[];  // visited bits, p.hub_n / 8 bytes
   const int gw = blockIdx.x * W + (threadIdx.x >> 5);
   const int P = gridDim.x * W;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) p.cta_smid[blockIdx.x] = sm_id();
+  __shared__ LevelCtrl s_ctrl;  // CTA 0 during a streak: the current level's control block
   int bar = 0, l = 0;
   long long acc[4] = {0, 0, 0, 0};  // reached, edges, candidates, work (leader)
   bool streak = false;           // CTA 0 is running small levels alone
   while (true) {
-    const int n_l = ld_relaxed(&p.st->ctrl[l & 1].n);
-    const int e_l = ld_relaxed(&p.st->ctrl[l & 1].e);
-    const bool bottom_up = ld_relaxed(&p.st->ctrl[l & 1].dir) != 0;
+    int n_l, e_l;
+    bool bottom_up;
+    if (streak) {
+      n_l = s_ctrl.n;
+      e_l = s_ctrl.e;
+      bottom_up = s_ctrl.dir != 0;
+    } else {
+      n_l = ld_relaxed(&p.st->ctrl[l & 1].n);
+      e_l = ld_relaxed(&p.st->ctrl[l & 1].e);
+      bottom_up = ld_relaxed(&p.st->ctrl[l & 1].dir) != 0;
+    }
     const bool small = n_l > 0 && p.small_edges > 0 && e_l <= p.small_edges && !bottom_up;
     if (streak && !small) {
       // CTA 0 ends its streak: the whole grid resumes at level l (or stops)
@@ -209,13 +239,21 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_level_loop(Param
       }
       continue;
     }
-    if (bottom_up) {
+    if (DO && bottom_up) {
       if (!bu_level<W>(p, l, n_l, e_l, &bar, acc)) break;
       ++l;
       continue;
     }
+    if (small && !streak) {
+      // a streak starts: its control blocks live in shared memory
+      if (threadIdx.x == 0) {
+        const LevelCtrl* c = &p.st->ctrl[l & 1];
+        s_ctrl = LevelCtrl{n_l, e_l, 0, ld_relaxed(&c->cum), 0, 0, 0, 0};
+      }
+      __syncthreads();
+    }
     streak = small;
-    if (!one_level<W>(p, l, n_l, e_l, &bar, s_hub, acc, !small)) {
+    if (!one_level<W>(p, l, n_l, e_l, &bar, s_hub, acc, !small, &s_ctrl)) {
       if (streak) {
         // release the parked CTAs; the error word makes everybody stop
         if (threadIdx.x == 0) st_relaxed(&p.st->resume_level, l);
@@ -475,10 +513,11 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   // CTA shape: one CTA of 32 warps per SM when the visited bits are in shared
   // memory (one copy per SM), else 8-warp CTAs (more SMs share a small level)
   const int cw = opts ? opts->cta_warps : 0;
-  if (cw != 0 && cw != 8 && cw != 32) return fail(BFS_E_INVAL, "cta_warps = %d: use 0, 8 or 32", cw);
+  if (cw != 0 && cw != 8 && cw != 16 && cw != 24 && cw != 32)
+    return fail(BFS_E_INVAL, "cta_warps = %d: use 0, 8, 16, 24 or 32", cw);
   g->wpc = cw ? cw : (g->hub_n > 0 ? 32 : 8);
   // persistent grid: every CTA that fits next to the shared-memory bits
-  const void* loop_fn = level_loop_fn(g->wpc);
+  const void* loop_fn = level_loop_fn(g->wpc, g->direction != 0);
   // the attribute is per kernel, shared by every graph: set it to the largest size any graph uses
   CUDA_TRY(cudaFuncSetAttribute(loop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(kHubMax)));
   int per_sm = 0;
@@ -628,7 +667,8 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
   if (g->persistent) {
     Params pc = p;
     void* args[] = {&pc};
-    CUDA_TRY(cudaLaunchCooperativeKernel(level_loop_fn(g->wpc), dim3(g->ctas), dim3(g->wpc * kWarp), args,
+    CUDA_TRY(cudaLaunchCooperativeKernel(level_loop_fn(g->wpc, p.direction != 0), dim3(g->ctas),
+                                         dim3(g->wpc * kWarp), args,
                                          loop_smem(p.hub_n), g->stream));
     ++g->launches;
   } else {
@@ -645,14 +685,22 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
       reached += n_l;
       edges += e_l;
       const int grid = std::max(1, (P_l + g->wpc - 1) / g->wpc);
-      if (g->wpc == 32) {
-        k_explore<32><<<grid, 32 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
-        CUDA_TRY(cudaGetLastError());
-        k_compact<32><<<grid, 32 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
-      } else {
-        k_explore<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
-        CUDA_TRY(cudaGetLastError());
-        k_compact<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+      switch (g->wpc) {
+        case 32:
+          k_explore<32><<<grid, 32 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+          k_compact<32><<<grid, 32 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+          break;
+        case 24:
+          k_explore<24><<<grid, 24 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+          k_compact<24><<<grid, 24 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+          break;
+        case 16:
+          k_explore<16><<<grid, 16 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+          k_compact<16><<<grid, 16 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
+          break;
+        default:
+          k_explore<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, n_l, e_l, P_l, C_l);
+          k_compact<8><<<grid, 8 * kWarp, 0, g->stream>>>(p, l, e_l, P_l, C_l);
       }
       CUDA_TRY(cudaGetLastError());
       g->launches += 2;
@@ -1044,7 +1092,7 @@ static int noalloc_setup(int dev, NoAllocDevice** out) {
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return fail(BFS_E_CUDA, "device %d has no cooperative launch", dev);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop<32>, 32 * kWarp, loop_smem(0)));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_loop<32, false>, 32 * kWarp, loop_smem(0)));
     if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
     d.scratch = static_cast<unsigned char*>(ptr);
     d.sms = sms;
@@ -1127,7 +1175,7 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   k_init<<<igrid, kThreads, 0, stream>>>(p, d->ctas);
   CUDA_TRY(cudaGetLastError());
   void* args[] = {&p};
-  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop<32>, dim3(d->ctas), dim3(32 * kWarp), args, loop_smem(0),
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_level_loop<32, false>, dim3(d->ctas), dim3(32 * kWarp), args, loop_smem(0),
                                        stream));
   DevState h;
   CUDA_TRY(cudaMemcpyAsync(&h, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));

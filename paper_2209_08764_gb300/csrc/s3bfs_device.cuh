@@ -299,10 +299,13 @@ __host__ __device__ inline void level_sizing(int e_l, int P, int grain, int work
 
 // ---------------------------------------------------------------------------
 // grid barrier without atomics: every CTA publishes its arrival in its own
-// word; CTA 0 waits for all of them and releases one word everybody waits on.
-// Every wait is bounded by the time limit and an iteration cap; on expiry the
-// error word is set and all CTAs return false.  Also returns false, in every
-// CTA, when any CTA raised an error before the barrier.
+// word; CTA 0 waits for all of them, then releases one word everybody waits
+// on.  The release word carries the error state: 2 * epoch + 1 when any CTA
+// raised an error before the barrier (or CTA 0's wait failed), so the
+// waiting CTAs learn it without another load.  Every wait is bounded by the
+// time limit and an iteration cap; on expiry the error word is set and all
+// CTAs return false.  Returns false, in every CTA, when any CTA raised an
+// error before the barrier.
 // ---------------------------------------------------------------------------
 template <class P>
 __device__ bool grid_sync(const P& p, int epoch) {
@@ -314,6 +317,7 @@ __device__ bool grid_sync(const P& p, int epoch) {
     __threadfence();
     if (!stall) st_relaxed(&p.bar_arrive[blockIdx.x], epoch);
   }
+  const unsigned target = (unsigned)epoch;
   if (blockIdx.x == 0) {
     // CTA 0 gathers the arrivals, four words per 16-byte load (the arrival
     // array is padded to a multiple of four entries)
@@ -329,34 +333,42 @@ __device__ bool grid_sync(const P& p, int epoch) {
         const bool done = (a.x >= epoch || base + 0 >= (int)gridDim.x) && (a.y >= epoch || base + 1 >= (int)gridDim.x) &&
                           (a.z >= epoch || base + 2 >= (int)gridDim.x) && (a.w >= epoch || base + 3 >= (int)gridDim.x);
         if (done) break;
-        if (ld_relaxed(&p.st->err) != 0) {
+        ++it;
+        if ((it & 31) == 0 && ld_relaxed(&p.st->err) != 0) {
           ok = false;
           break;
         }
-        if (++it > kSpinIters || global_ns() - t0 > p.spin_ns) {
+        if (it > kSpinIters || global_ns() - t0 > p.spin_ns) {
           set_err(p, BFS_E_TIMEOUT, 1);
           ok = false;
           break;
         }
-        if (it > 64) __nanosleep(100);
+        if (it > 64) __nanosleep(64);
       }
     }
     ok = __syncthreads_and(ok);
-    if (threadIdx.x == 0 && ok) {
-      __threadfence();
-      st_relaxed(&p.st->bar_release, epoch);
+    if (threadIdx.x == 0) {
+      __threadfence();  // the arrivals seen above happen before the error check
+      const bool err = !ok || ld_relaxed(&p.st->err) != 0;
+      st_relaxed(&p.st->bar_release, (int)(2u * target + (err ? 1u : 0u)));
+      s_ok = !err;
     }
-  }
-  if (threadIdx.x == 0) {
+  } else if (threadIdx.x == 0) {
     int ok = 1, it = 0;
     long long t0 = global_ns();
     int prog = ld_relaxed(&p.st->progress);
-    while (ld_acquire(&p.st->bar_release) < epoch) {
-      if (ld_relaxed(&p.st->err) != 0) {
-        ok = 0;
+    while (true) {
+      const unsigned r = (unsigned)ld_acquire(&p.st->bar_release);
+      if ((r >> 1) >= target) {
+        ok = (r & 1u) == 0;
         break;
       }
-      if ((it & 127) == 127) {
+      ++it;
+      if ((it & 31) == 0) {
+        if (ld_relaxed(&p.st->err) != 0) {
+          ok = 0;
+          break;
+        }
         // CTA 0 working alone through small levels is progress, not a stall
         const int pr = ld_relaxed(&p.st->progress);
         if (pr != prog) {
@@ -365,7 +377,7 @@ __device__ bool grid_sync(const P& p, int epoch) {
           it = 0;
         }
       }
-      if (++it > kSpinIters || global_ns() - t0 > p.spin_ns) {
+      if (it > kSpinIters || global_ns() - t0 > p.spin_ns) {
         set_err(p, BFS_E_TIMEOUT, 2);
         ok = 0;
         break;
@@ -373,9 +385,7 @@ __device__ bool grid_sync(const P& p, int epoch) {
       if (it > 64) __nanosleep(64);
     }
     __threadfence();
-    // one decision per CTA: an error raised before the barrier by any CTA
-    // (a timeout, or a frontier larger than n) makes every CTA leave
-    s_ok = ok && ld_relaxed(&p.st->err) == 0;
+    s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
@@ -396,7 +406,11 @@ __device__ __forceinline__ int emit(int2* out, int cnt, bool k, int v, int u, in
 // s_hub / hub_lim: visited bits of vertices [0, hub_lim) in shared memory, a
 // snapshot taken at the start of the level (hub_lim = 0: none).  A set bit
 // means the vertex already has a level, so its level[] test is skipped.
-__device__ inline int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, int e_begin, int e_end,
+#ifndef S3BFS_EXPLORE_QUAL
+#define S3BFS_EXPLORE_QUAL inline
+#endif
+__device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, int e_begin,
+                                                int e_end,
                              int2* out, const uint32_t* s_hub, int hub_lim) {
   const int lane = threadIdx.x & (kWarp - 1);
   // (selects, not p.EX[par]: a runtime index into the parameter block would
@@ -571,9 +585,15 @@ constexpr int kCompactR = S3BFS_CR;
 // b: rank of this CTA among the CTAs that hold the level's chunks (the scan
 // runs over ranks 0 .. (P_l - 1) / W).  work: neighbour entries this warp
 // examined in the level (summed into the next level's control block).
+// s_next (optional, shared memory): the publishing thread also leaves the
+// next level's control block there (n = -1 when it raised an error), for a
+// CTA that runs the next level alone.
+#ifndef S3BFS_COMPACT_QUAL
+#define S3BFS_COMPACT_QUAL
+#endif
 template <int W>  // warps per CTA
-__device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt, int b,
-                            int work) {
+__device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand, int* aux, int cnt, int b,
+                            int work, LevelCtrl* s_next = nullptr) {
   __shared__ int sK[W], sD[W], sC[W], sW[W];
   __shared__ int sRed[4][W];
   __shared__ int sPre[4];
@@ -755,20 +775,26 @@ __device__ bool compact_cta(const Params& p, int l, int par, int P_l, int2* cand
       c_l += sC[w];
       w_l += sW[w];
     }
-    const long long cum = (long long)ld_relaxed(&p.st->ctrl[par].cum) + e_next;
+    const LevelCtrl cur = s_next ? *s_next : LevelCtrl{ld_relaxed(&p.st->ctrl[par].n), 0, 0,
+                                                         ld_relaxed(&p.st->ctrl[par].cum),
+                                                         ld_relaxed(&p.st->ctrl[par].dir), 0, 0, 0};
+    const long long cum = (long long)cur.cum + e_next;
     if (n_next > p.n || e_next > p.nnz || e_next < 0 || cum > p.nnz) {
       set_err(p, BFS_E_MULTIGRAPH, 4);
+      if (s_next) s_next->n = -1;
     } else {
       EXn[n_next] = (int)e_next;
-      const int dir_l = ld_relaxed(&p.st->ctrl[par].dir);
+      const int dir_l = cur.dir;
+      const int dir_next = next_direction(p, dir_l, cur.n, n_next, e_next, cum);
       LevelCtrl* c = &p.st->ctrl[np];
       st_relaxed(&c->n, (int)n_next);
       st_relaxed(&c->e, (int)e_next);
       st_relaxed(&c->c, (int)c_l);
       st_relaxed(&c->cum, (int)cum);
-      st_relaxed(&c->dir, next_direction(p, dir_l, ld_relaxed(&p.st->ctrl[par].n), n_next, e_next, cum));
+      st_relaxed(&c->dir, dir_next);
       st_relaxed(&c->fb, dir_l);
       st_relaxed(&c->w, (int)w_l);
+      if (s_next) *s_next = LevelCtrl{(int)n_next, (int)e_next, (int)c_l, (int)cum, dir_next, dir_l, (int)w_l, 0};
       if (l < p.lvl_cap) {
         p.lvl[(long long)l * kLevelFields + 2] = (int)c_l;
         p.lvl[(long long)l * kLevelFields + 8] = (int)w_l;
@@ -801,7 +827,16 @@ __device__ __forceinline__ void level_bits(const Params& p, int l, int words, ui
 // Visited bits of vertices [0, hub_n), from the level array after a level's
 // explore (all its level stores are visible).
 __device__ __forceinline__ void build_hub_bits(const Params& p, int gw, int P) {
+#if S3BFS_HUB_BITS_WORDWISE
+  const int lane = threadIdx.x & (kWarp - 1);
+  for (int w = gw; w < (p.hub_n >> 5); w += P) {
+    const int lv = ld_relaxed_nb(p.level + (w << 5) + lane);
+    const unsigned m = __ballot_sync(kFull, lv >= 0);
+    if (lane == 0) p.hub_bits[w] = m;
+  }
+#else
   level_bits(p, -1, p.hub_n >> 5, p.hub_bits, gw, P);
+#endif
 }
 
 // Copies the visited bits into shared memory (whole CTA); returns hub_n.

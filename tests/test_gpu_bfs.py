@@ -108,6 +108,8 @@ def test_rmat16_64_sources(rmat16):
     dict(small_level_edges=1 << 22, relabel=1), dict(small_level_edges=-1, relabel=-1),
     dict(cta_warps=8), dict(cta_warps=8, ctas=3), dict(cta_warps=8, small_level_edges=-1),
     dict(cta_warps=8, persistent=-1), dict(cta_warps=32, relabel=-1), dict(cta_warps=8, relabel=1),
+    dict(cta_warps=16), dict(cta_warps=24), dict(cta_warps=16, relabel=-1, ctas=5),
+    dict(cta_warps=24, persistent=-1), dict(cta_warps=16, small_level_edges=-1),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_rmat16_launch_configurations(rmat16, opts):
     rp, ci, srcs, keys = rmat16
@@ -223,7 +225,7 @@ def test_run_batch_matches_single_runs(rmat16, relabel):
 
 
 @pytest.mark.parametrize("small", [-1, 0, 1 << 20])
-@pytest.mark.parametrize("cw", [8, 32])
+@pytest.mark.parametrize("cw", [8, 16, 32])
 def test_long_path_and_grid_small_level_mode(small, cw):
     """Thousands of tiny levels: CTA 0 alone runs them (small-level mode), or
     the whole grid with two grid barriers per level (small = -1)."""

@@ -66,6 +66,8 @@ def test_rmat16_direction_optimising(rmat16, relabel):
     dict(do_alpha=1 << 20, do_beta=1),         # and never back
     dict(do_alpha=2, do_beta=1 << 20),         # late switch, early switch back
     dict(do_alpha=1 << 20, cta_warps=8),
+    dict(do_alpha=1 << 20, cta_warps=16),
+    dict(do_alpha=1 << 20, cta_warps=24),
     dict(do_alpha=1 << 20, ctas=3),            # few warps: many words per warp
     dict(do_alpha=1 << 20, ctas=1, cta_warps=8),
     dict(do_alpha=1 << 20, small_level_edges=-1),
