@@ -131,6 +131,57 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
+class EnergyMeter:
+    """GPU energy from NVML's total-energy counter (millijoules since the
+    driver loaded), read through ctypes; every reading is None where NVML is
+    not available.  Reading the counter changes nothing on the GPU."""
+
+    def __init__(self, torch, dev):
+        self.lib = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            bus = getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", None)
+            dom = getattr(torch.cuda.get_device_properties(dev), "pci_domain_id", 0)
+            ok = False
+            if bus is not None:
+                key = f"{dom:08x}:{bus:02x}:00.0".encode()
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(key, ctypes.byref(h)) == 0
+            if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(dev), ctypes.byref(h)) != 0:
+                return
+            self.lib, self.h = lib, h
+        except (OSError, AttributeError):
+            self.lib = None
+
+    def read_mj(self):
+        if self.lib is None:
+            return None
+        e = ctypes.c_ulonglong()
+        return e.value if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.h, ctypes.byref(e)) == 0 else None
+
+
+def energy_per_traversal(meter, run_one, srcs, seconds=1.5):
+    """Joules per traversal and mean power over >= seconds of back-to-back
+    traversals of the sources (NVML energy counter around the loop)."""
+    import torch
+    if meter is None or meter.read_mj() is None:
+        return None
+    torch.cuda.synchronize()
+    e0, t0, k = meter.read_mj(), time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds:
+        for s in srcs:
+            run_one(int(s))
+            k += 1
+    torch.cuda.synchronize()
+    e1, t1 = meter.read_mj(), time.perf_counter()
+    if e1 is None or e1 <= e0:
+        return None
+    return {"j_per_traversal": (e1 - e0) * 1e-3 / k, "avg_w": (e1 - e0) * 1e-3 / (t1 - t0),
+            "traversals": k, "seconds": round(t1 - t0, 2), "source": "NVML total energy counter"}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -425,6 +476,9 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="choose the options by the autotuner (coordinate descent on 4 of the sources)")
     ap.add_argument("--tune-cache", default="", help="JSON cache file of the autotuner")
+    ap.add_argument("--with-wi", type=int, default=1,
+                    help="1 (default): add the work-insensitive arm (every warp at every level) to the line")
+    ap.add_argument("--no-energy", action="store_true", help="skip the NVML energy-per-traversal loop")
     ap.add_argument("--with-do", type=int, default=1,
                     help="1 (default): add a direction-optimising run of the same sources to the top-down line")
     ap.add_argument("--batch", action="store_true",
@@ -488,6 +542,15 @@ def main():
         do = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, 1, summary=True)
         do["speedup_vs_top_down"] = round(do["value"] / line["value"], 3)
         line["direction_optimising"] = do
+    if rank == 0 and not direction and args.with_wi and not args.work_insensitive:
+        # the paper's comparison arm: every warp active at every level
+        wi = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, 0, summary=True,
+                            tuned=dict(tuned or {}, work_insensitive=1))
+        wi["time_ratio_vs_work_sensitive"] = round(wi["ms_level_step_median"] / line["ms_level_step_median"], 3)
+        e_ws, e_wi = (line.get("energy") or {}), (wi.get("energy") or {})
+        if e_ws.get("j_per_traversal") and e_wi.get("j_per_traversal"):
+            wi["energy_ratio_vs_work_sensitive"] = round(e_wi["j_per_traversal"] / e_ws["j_per_traversal"], 3)
+        line["work_insensitive"] = wi
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, rp, ci, srcs, args.cpu_budget)
@@ -616,6 +679,9 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "avg_launch_ms": float(ms_loop.mean())}
     hmean = len(ms_loop) / np.sum(ms_loop / 1e3 / np.tile(teps_edges, args.steps)) / 1e9
     launches = int(recs[:, 7].sum())
+    energy = None
+    if not args.no_energy and rank == 0:
+        energy = energy_per_traversal(EnergyMeter(torch, dev), lambda s: B.bfs_run(g, s, level, parent, None), srcs)
     if summary:
         B.bfs_destroy(g)
         return {"value": round(gteps, 3), "unit": "GTEPS", "ms_per_step": ms_max / args.steps,
@@ -623,8 +689,9 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "bottom_up_levels_median": float(np.median(bu_levels)),
                 "work_edges_per_traversal": float(recs[:, 8].mean()),
                 "edges_scanned_per_traversal": float(recs[:, 3].mean()),
-                "gpu_launches": launches, "clocks": clk.summary(),
-                "options": {"alpha": 15, "beta": 18}, "create_s": round(t_create, 2)}
+                "gpu_launches": launches, "clocks": clk.summary(), "energy": energy,
+                "options": {f: getattr(opts, f) for f, _ in opts._fields_ if getattr(opts, f)},
+                "create_s": round(t_create, 2)}
 
     # end to end through the C ABI with pinned host outputs (copies inside the timed region)
     e2e = None
@@ -670,6 +737,7 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "ctas": info["ctas"], "warps": info["warps"]}
         if e2e:
             line["e2e"] = e2e
+        line["energy"] = energy
         if per_level:
             line["per_level"] = per_level
     B.bfs_destroy(g)

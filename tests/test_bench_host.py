@@ -1,0 +1,44 @@
+"""Host-side pieces of bench.py (CPU): the level-loop byte model, the energy
+meter's fallback without NVML, and the workload registry."""
+import numpy as np
+
+import bench
+
+
+def _row(n_l, e_l, c_l, direction=0, work=None):
+    # per-level record: n_l, e_l, c_l, active_warps, active_sms, ns, ns_explore, direction, work
+    return [n_l, e_l, c_l, 0, 0, 0, 0, direction, e_l if work is None else work]
+
+
+def test_top_down_byte_model():
+    rows = [_row(1, 3, 3), _row(3, 10, 5), _row(4, 0, 0)]
+    # 8 per edge scanned + 32 per frontier vertex + 28 per candidate
+    assert bench.level_bytes(100, rows) == 8 * 13 + 32 * 8 + 28 * 8
+
+
+def test_bottom_up_byte_model():
+    n = 1000
+    rows = [_row(1, 50, 40), _row(40, 900, 300, direction=1, work=700), _row(300, 2000, 10, direction=1, work=50)]
+    got = bench.level_bytes(n, rows)
+    td = 8 * 50 + 32 * 1 + 28 * 40
+    # first bottom-up level: visited 41 after it; it also pays the bitmap build
+    bu1 = 4 * n + 8 * (n - 41) + 8 * 700 + n / 8 + 36 * 300 + 4 * n + n / 8
+    bu2 = 4 * n + 8 * (n - 341) + 8 * 50 + n / 8 + 36 * 10
+    assert np.isclose(got, td + bu1 + bu2)
+
+
+def test_energy_meter_without_nvml_is_none(monkeypatch):
+    class NoNvml:
+        lib = None
+
+        def read_mj(self):
+            return None
+    assert bench.energy_per_traversal(NoNvml(), lambda s: None, [1, 2], seconds=0.01) is None
+    assert bench.energy_per_traversal(None, lambda s: None, [1], seconds=0.01) is None
+
+
+def test_workloads_are_the_documented_configurations():
+    w = bench.WORKLOADS["rmat22"]
+    assert (w["scale"], w["edgefactor"], w["sources"], w["seed"], w["src_seed"]) == (22, 16, 64, 1, 2)
+    assert bench.WORKLOADS["grid4096"]["rows"] == bench.WORKLOADS["grid4096"]["cols"] == 4096
+    assert bench.WORKLOADS["er20"]["m"] == 8 << 20
