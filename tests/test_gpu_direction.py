@@ -13,7 +13,7 @@ import pytest
 
 import graphgen
 import oracle
-from gpu_helpers import Dev, check_against_oracle, expected_directions
+from gpu_helpers import Dev, check_against_oracle
 from paper_2209_08764_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
@@ -36,13 +36,6 @@ def _cuda():
 def rmat16():
     rp, ci = graphgen.rmat(16, 16, seed=1)
     return rp, ci, oracle.Oracle(rp, ci)
-
-
-def _dirs(rp, ci, src, **o):
-    lv, _ = oracle.bfs(rp, ci, src)
-    n_l, e_l = oracle.level_profile(rp, lv)
-    return expected_directions(len(rp) - 1, len(ci), n_l, e_l, 1, o.get("do_alpha", 0) or 15,
-                               o.get("do_beta", 0) or 18)
 
 
 @pytest.mark.parametrize("relabel", [0, 1, -1])
@@ -158,12 +151,3 @@ def test_launch_per_phase_stays_top_down(rmat16):
             assert (pl[:, 7] == 0).all()
     finally:
         d.close()
-
-
-def test_direction_rule_on_rmat16_profile(rmat16):
-    # the default alpha / beta switch an R-MAT traversal to bottom-up for its
-    # middle levels and back for its tail (the property the option exists for)
-    rp, ci, _ = rmat16
-    s = int(graphgen.sample_sources(rp, 1, seed=2)[0])
-    d = _dirs(rp, ci, s)
-    assert d[0] == 0 and d.max() == 1 and d[-1] == 0
