@@ -58,9 +58,6 @@
 #ifndef S3BFS_HUB_LOG2
 #define S3BFS_HUB_LOG2 18  // visited bits in shared memory for up to 2^this vertices
 #endif
-#ifndef S3BFS_CLAIM_PARENT
-#define S3BFS_CLAIM_PARENT 0  // 1: explore tests and claims parent[] only; the compaction writes level[]
-#endif
 #ifndef S3BFS_MIN_CTAS
 #define S3BFS_MIN_CTAS 1  // __launch_bounds__ minimum CTAs per SM of the level loop (64 registers)
 #endif
@@ -526,7 +523,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
         for (int j = 0; j < 4; ++j) {
           const bool known = cc[j] < hub_lim && ((s_hub[cc[j] >> 5] >> (cc[j] & 31)) & 1u);
           vv[r][j] = pos[r] + j >= wp0[r] && pos[r] + j < wp1[r] && !known;
-          lv[r][j] = vv[r][j] ? ld_level((S3BFS_CLAIM_PARENT ? parent : level) + cc[j]) : 0;
+          lv[r][j] = vv[r][j] ? ld_level(level + cc[j]) : 0;
         }
       }
 #pragma unroll
@@ -536,7 +533,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
         for (int j = 0; j < 4; ++j) {
           const bool k = vv[r][j] && lv[r][j] < 0;
           if (k) {
-            if (!S3BFS_CLAIM_PARENT) st_relaxed(level + cc[j], lnext);
+            st_relaxed(level + cc[j], lnext);
             st_relaxed(parent + cc[j], wu[r]);
           }
           cnt = emit(out, cnt, k, cc[j], wu[r], lane);
@@ -629,7 +626,6 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
     for (int r = 0; r < kCompactR; ++r) {
       keep[r] = pv[r] == pr[r].y;
       v[r] = pr[r].x;
-      if (S3BFS_CLAIM_PARENT && keep[r]) p.level[v[r]] = l + 1;
       rs[r] = keep[r] ? __ldg(p.row_ptr + v[r]) : 0;
       re[r] = keep[r] ? __ldg(p.row_ptr + v[r] + 1) : 0;
     }
@@ -809,8 +805,7 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
 }
 
 // Bits of vertices [0, 32 * words) from the level array: bit v set iff
-// level[v] == l, or iff v is visited when l < 0 (level[v] >= 0; parent[v] >=
-// 0 when the explore claims through parent[] alone).  A warp writes
+// level[v] == l, or iff level[v] >= 0 (visited) when l < 0.  A warp writes
 // four words at a time (four coalesced loads in flight per lane, one ballot
 // per word); words is a multiple of 4.  Every word is written.
 __device__ __forceinline__ void level_bits(const Params& p, int l, int words, uint32_t* out, int gw, int P) {
@@ -820,7 +815,7 @@ __device__ __forceinline__ void level_bits(const Params& p, int l, int words, ui
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int v = (q << 7) + (j << 5) + lane;
-      lv[j] = v < p.n ? ld_relaxed_nb((l < 0 && S3BFS_CLAIM_PARENT ? p.parent : p.level) + v) : -1;
+      lv[j] = v < p.n ? ld_relaxed_nb(p.level + v) : -1;
     }
     unsigned m[4];
 #pragma unroll
