@@ -405,6 +405,7 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
     # the server, in real time
     so = B.bfs_server_opts()
     so.slots = args.serve_slots
+    so.local_levels = args.serve_local_levels
     srv = B.bfs_server_create(handles, so, stream.cuda_stream)
     done = {}
     nxt = 0
@@ -435,7 +436,7 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serving-pool32", "graphs": [g[0] for g in graphs], "queries": N,
                        "load": load if load > 0 else "all at t=0", "lambda_qps": lam if load > 0 else None,
-                       "slots": args.serve_slots,
+                       "slots": args.serve_slots, "local_levels": args.serve_local_levels,
                        "arrivals": "Poisson, graph uniform over the pool, source uniform over non-isolated, seed 5"},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "mean": float(lat.mean() * 1e3)},
@@ -491,6 +492,8 @@ def main():
                     help="arrival rates as fractions of the one-at-a-time capacity, comma-separated; "
                          "0 = every query at t = 0 (saturation throughput)")
     ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-local-levels", type=int, default=0,
+                    help="bfs_server_opts.local_levels: 0 default (8), -1 off")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.sources:

@@ -76,7 +76,7 @@ class bfs_server_opts(ctypes.Structure):
         ("chunk_edges", ctypes.c_int32),
         ("cta_warps", ctypes.c_int32),
         ("spin_limit_ms", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("local_levels", ctypes.c_int32),
         ("arena_bytes", ctypes.c_int64),
     ]
 

@@ -34,6 +34,10 @@ struct ServeParams {
   int32_t nslots;
   int32_t max_levels;  // levels per launch
   int32_t grain;
+  // a query with one CTA and a level of at most local_edges edges runs up to
+  // local_levels levels per step alone, with CTA barriers (0: off)
+  int32_t local_levels;
+  int32_t local_edges;
   int32_t* finished;   // set when a query finished during this launch
   // grid barrier state of the server
   DevState* st;
@@ -85,6 +89,58 @@ __device__ __forceinline__ void serve_assign(const ServeParams& sp, long long* s
   }
 }
 
+// Levels of one query run by this CTA alone (the query got one CTA and its
+// levels are small): explore, CTA barrier, compaction, CTA barrier, slot
+// update, up to sp.local_levels levels or until a level is no longer small or
+// the query ends.  The rest of the grid meanwhile runs its own queries' level
+// and waits at the step's grid barrier.
+template <int W>
+__device__ void serve_local(const ServeParams& sp, SlotDev* sd) {
+  __shared__ int s_go;
+  const Params& p = sd->p;
+  const int wib = threadIdx.x >> 5;
+  for (int k = 0; k < sp.local_levels; ++k) {
+    const int l = ld_relaxed(&sd->level);
+    const int par = l & 1;
+    const int n_l = ld_relaxed(&p.st->ctrl[par].n);
+    const int e_l = ld_relaxed(&p.st->ctrl[par].e);
+    if (n_l <= 0 || e_l > sp.local_edges) break;  // uniform: every thread read the same words
+    int P_l, C_l;
+    level_sizing(e_l, W, sp.grain, 0, &P_l, &C_l);
+    int cnt = 0, e_begin = 0, work = 0;
+    if (wib < P_l) {
+      const long long eb = (long long)wib * C_l;
+      e_begin = (int)min(eb, (long long)e_l);
+      const int e_end = (int)min(eb + C_l, (long long)e_l);
+      work = e_end - e_begin;
+      if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
+    }
+    __syncthreads();
+    if (P_l == 0) {
+      if (threadIdx.x == 0) publish_empty_next(p, par);
+    } else {
+      compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, 0, work);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int n_next = ld_relaxed(&p.st->ctrl[par ^ 1].n);
+      sd->reached += n_l;
+      sd->edges += e_l;
+      sd->cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
+      sd->num_levels = l + 1;
+      st_relaxed(&sd->level, l + 1);
+      const bool done = n_next <= 0 || ld_relaxed(&p.st->err) != 0;
+      if (done) {
+        st_relaxed(&sd->active, 0);
+        st_relaxed(sp.finished, 1);
+      }
+      s_go = !done;
+    }
+    __syncthreads();
+    if (!s_go) break;
+  }
+}
+
 // One launch: up to sp.max_levels levels of every running query.
 template <int W>
 __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParams sp) {
@@ -99,6 +155,16 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
     __syncthreads();
     if (q == -2) break;  // same decision in every CTA: they read the same slot states
     SlotDev* sd = q >= 0 ? sp.slots + q : nullptr;
+    // a query alone on this CTA with a small level: several levels now, alone
+    bool local = false;
+    if (sd && gsize == 1 && sp.local_levels > 0) {
+      const int l0 = ld_relaxed(&sd->level);
+      local = ld_relaxed(&sd->p.st->ctrl[l0 & 1].e) <= sp.local_edges;
+    }
+    if (local) {
+      serve_local<W>(sp, sd);
+      sd = nullptr;  // nothing left for this step's shared phases
+    }
     int l = 0, par = 0, n_l = 0, e_l = 0, P_l = 0, C_l = 0, cnt = 0, e_begin = 0, work = 0;
     if (sd) {
       const Params& p = sd->p;
