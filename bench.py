@@ -406,6 +406,7 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
     so = B.bfs_server_opts()
     so.slots = args.serve_slots
     so.local_levels = args.serve_local_levels
+    so.levels_per_launch = args.serve_levels_per_launch
     srv = B.bfs_server_create(handles, so, stream.cuda_stream)
     done = {}
     nxt = 0
@@ -437,6 +438,7 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
             "config": {"workload": "serving-pool32", "graphs": [g[0] for g in graphs], "queries": N,
                        "load": load if load > 0 else "all at t=0", "lambda_qps": lam if load > 0 else None,
                        "slots": args.serve_slots, "local_levels": args.serve_local_levels,
+                       "levels_per_launch": args.serve_levels_per_launch or 8,
                        "arrivals": "Poisson, graph uniform over the pool, source uniform over non-isolated, seed 5"},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "mean": float(lat.mean() * 1e3)},
@@ -492,8 +494,10 @@ def main():
                     help="arrival rates as fractions of the one-at-a-time capacity, comma-separated; "
                          "0 = every query at t = 0 (saturation throughput)")
     ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-levels-per-launch", type=int, default=0,
+                    help="bfs_server_opts.levels_per_launch (0 = the library default, 8)")
     ap.add_argument("--serve-local-levels", type=int, default=0,
-                    help="bfs_server_opts.local_levels: 0 default (8), -1 off")
+                    help="bfs_server_opts.local_levels (0 = off)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.sources:

@@ -263,10 +263,11 @@ typedef struct bfs_server_opts {
   int32_t chunk_edges;       /* grain, as bfs_opts.chunk_edges; 0 = 64 */
   int32_t cta_warps;         /* 8 or 32 warps per CTA; 0 = 8 */
   int32_t spin_limit_ms;     /* device wait limit; 0 = 1000 */
-  int32_t local_levels;      /* a query that gets one CTA and whose level has at most 256
-                                edges per warp runs up to this many levels per step on
-                                that CTA alone, with CTA barriers (deep queries with small
-                                frontiers advance that much faster); 0 = 8, -1 = off */
+  int32_t local_levels;      /* > 0: a query that gets one CTA and whose level has at most
+                                256 edges per warp runs up to this many levels per step on
+                                that CTA alone, with CTA barriers; 0 = off (the default:
+                                on the serving pool it did not lower p99 and it cut the
+                                saturated throughput) */
   int64_t arena_bytes;       /* device memory for the working buffers of running
                                 queries (admission waits while it is full);
                                 0 = half of the free memory, at most 32 GiB */

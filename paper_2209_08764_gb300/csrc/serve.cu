@@ -112,7 +112,7 @@ struct bfs_server {
   cudaStream_t stream = nullptr;
   int sms = 0, wpc = 8, ctas = 0;
   int nslots = 64, levels_per_launch = 8, grain = 64;
-  int local_levels = 8;
+  int local_levels = 0;
   long long spin_ns = 1000000000ll;
   std::vector<bfs_graph*> graphs;
   Arena arena;
@@ -184,7 +184,6 @@ static int server_create_impl(bfs_server* s, bfs_graph* const* graphs, int32_t n
     if (opts->spin_limit_ms > 0) s->spin_ns = (long long)opts->spin_limit_ms * 1000000ll;
     if (opts->arena_bytes > 0) arena_bytes = (size_t)opts->arena_bytes;
     if (opts->local_levels > 0) s->local_levels = opts->local_levels;
-    if (opts->local_levels < 0) s->local_levels = 0;
   }
   if (s->nslots > kMaxSlots) return fail(BFS_E_INVAL, "slots = %d: at most %d", s->nslots, kMaxSlots);
   if (s->wpc != 8 && s->wpc != 32) return fail(BFS_E_INVAL, "cta_warps = %d: use 8 or 32", s->wpc);
