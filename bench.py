@@ -68,11 +68,22 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def strip_c_comments(src: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed, so
+    that an edit of comments alone leaves the hash below unchanged."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_source_hash():
+    """First 16 hex digits of the sha256 of the level-loop sources (comments
+    stripped): the key under which a committed ncu summary is valid."""
     h = hashlib.sha256()
     for f in ("paper_2209_08764_gb300/csrc/s3bfs.cu", "paper_2209_08764_gb300/csrc/s3bfs_device.cuh"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(strip_c_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -48,7 +48,7 @@ extern "C" {
 typedef struct bfs_opts {
   int32_t chunk_edges;      /* grain: minimum edges per warp chunk.  Level l runs
                                P_l = min(P, ceil(e_l / chunk_edges)) warps, the
-                               work-sensitive count of Fig. 1 lines 11/16 (the
+                               work-sensitive thread count of Fig. 1 (the
                                paper's own formula is chunk_edges = 1).  Default 64 */
   int32_t ctas;             /* persistent grid size G in CTAs; 0 = every CTA that can be
                                co-resident on the device */
@@ -137,7 +137,7 @@ typedef struct bfs_graph bfs_graph; /* opaque; owned by the library */
  * an undirected graph is given with both directions.  The graph must be
  * simple within each row (no repeated neighbour): the dedup step keeps a
  * candidate (v, u) when parent[v] still equals u after the level, which is
- * unique per v only if u reaches v by one edge (Fig. 1 lines 19-23 with the
+ * unique per v only if u reaches v by one edge (Fig. 1's owner check, with the
  * owner id taken to be the parent vertex).  Self-loops are harmless.
  *
  * Ownership: the CSR is COPIED into library-owned device memory; the caller

@@ -13,12 +13,12 @@ Contents
 ``check_bfs_tree``   validity of any parent array against the levels (a parent
                      sits one level up and the tree edge exists).
 ``level_profile``    per-level frontier size n_l and edge count e_l implied by
-                     a level array (Fig. 1 lines 9 and 12-15).
+                     a level array (Fig. 1's main loop, degree gather and EdgeSum).
 ``s3bfs_fig1``       Fig. 1 itself, step by step in the paper's order and
                      notation (numpy per step), for per-level quantities:
                      n_l, e_l, P_l, the start points, candidates and Sizes.
 ``start_points_scatter`` / ``start_points_bsearch``
-                     Find-StartExpPoint (Fig. 1 line 17) in the paper's range-
+                     Find-StartExpPoint (Fig. 1) in the paper's range-
                      scatter form (Analysis, last paragraph) and in the binary
                      search form it replaces.
 """
@@ -37,7 +37,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-INF = -1  # the oracle writes -1 where the paper writes infinity (Fig. 1 line 3)
+INF = -1  # the oracle writes -1 where the paper writes infinity (Fig. 1, initialisation)
 
 
 def build(force: bool = False) -> str:
@@ -132,7 +132,7 @@ def check_bfs_tree(row_ptr, col_idx, src: int, level, parent, keys: np.ndarray |
 
 def level_profile(row_ptr, level) -> tuple[np.ndarray, np.ndarray]:
     """(n_l, e_l) for l = 0..L-1: vertices at distance l, and the sum of their
-    out-degrees (the edges level l explores, Fig. 1 lines 12-15)."""
+    out-degrees (the edges level l explores: Fig. 1's EdgeSum total e_l)."""
     level = np.asarray(level)
     deg = np.diff(np.asarray(row_ptr, np.int64))
     r = level >= 0
@@ -189,7 +189,7 @@ def s3bfs_fig1(row_ptr, col_idx, s: int, P: int, grain: int = 1, race: str = "ma
     of the main loop (frontier = vertices at distance k).
 
     ``grain`` is the minimum number of edges per thread: P_l = min(P,
-    ceil(e_l / grain)); grain = 1 is line 16 exactly.  Thread i explores edges
+    ceil(e_l / grain)); grain = 1 is Fig. 1's thread count exactly.  Thread i explores edges
     [i*C, min((i+1)*C, e_l)) with C = ceil(e_l / P_l), the "(almost) equal
     division" of the Algorithm paragraph.
 
@@ -205,7 +205,7 @@ def s3bfs_fig1(row_ptr, col_idx, s: int, P: int, grain: int = 1, race: str = "ma
     ci = np.asarray(col_idx, np.int64)
     n = len(rp) - 1
     Degree = np.diff(rp)
-    # lines 1-8: initialisation
+    # initialisation
     d = np.full(n, INF, np.int64)
     Owner = np.full(n, P, np.int64)
     d[s] = 0
@@ -213,11 +213,11 @@ def s3bfs_fig1(row_ptr, col_idx, s: int, P: int, grain: int = 1, race: str = "ma
     CurLevelVertices = np.array([s], np.int64)
     l = 0
     levels = []
-    # line 9: main loop while the frontier is non-empty
+    # main loop while the frontier is non-empty
     while len(CurLevelVertices) > 0:
         n_l = len(CurLevelVertices)
-        l += 1                                               # line 10
-        # lines 12-13: degree gather; line 14: prefix sum; line 15: e_l
+        l += 1                                               # next level
+        # degree gather; prefix sum (EdgeSum); its last entry e_l
         EdgeSum = np.cumsum(Degree[CurLevelVertices])
         e_l = int(EdgeSum[-1])
         rec = {"n_l": n_l, "e_l": e_l, "frontier": CurLevelVertices.copy()}
@@ -226,11 +226,11 @@ def s3bfs_fig1(row_ptr, col_idx, s: int, P: int, grain: int = 1, race: str = "ma
                        Sizes=np.zeros(0, np.int64))
             levels.append(rec)
             break
-        P_l = min(P, -(-e_l // grain))                       # line 16 (grain 1: min(P, e_l))
+        P_l = min(P, -(-e_l // grain))                       # thread count (grain 1: min(P, e_l))
         C = -(-e_l // P_l)
-        # line 17: Find-StartExpPoint
+        # Find-StartExpPoint
         starts = start_points_scatter(EdgeSum, e_l, P_l, C)
-        # line 18: EXPLORE-VERTEX over every thread's edge segment
+        # EXPLORE-VERTEX over every thread's edge segment
         ex = np.concatenate([[0], EdgeSum[:-1]])
         u_idx = np.repeat(np.arange(n_l), Degree[CurLevelVertices])
         u = CurLevelVertices[u_idx]
@@ -259,10 +259,10 @@ def s3bfs_fig1(row_ptr, col_idx, s: int, P: int, grain: int = 1, race: str = "ma
         # order (the largest i) is the one that remains
         Owner[v[ce]] = -1
         np.maximum.at(Owner, v[ce], thread[ce])
-        # lines 19-23: each thread keeps the vertices it still owns
+        # owner check: each thread keeps the vertices it still owns
         keep = ce[Owner[v[ce]] == thread[ce]]
         Sizes = np.bincount(thread[keep], minlength=P_l)
-        # line 24: prefix sum of Sizes; lines 25-29: linearisation
+        # prefix sum of Sizes, then linearisation
         Sizes_incl = np.cumsum(Sizes)
         order = np.argsort(thread[keep], kind="stable")
         CurLevelVertices = v[keep][order]

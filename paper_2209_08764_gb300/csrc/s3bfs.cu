@@ -48,7 +48,7 @@ static const void* level_loop_fn(int wpc, bool DO) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// a0 (Fig. 1 lines 1-8): level = parent = -1 except level[s] = 0, parent[s] =
+// a0 (Fig. 1, initialisation): level = parent = -1 except level[s] = 0, parent[s] =
 // s; F_0 = [s] with its row start and degree; clear the scan and barrier state.
 __global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) { init_traversal(p, ctas); }
 

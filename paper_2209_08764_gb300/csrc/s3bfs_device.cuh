@@ -1,26 +1,26 @@
 // S3BFS level step on sm_103a: device code.
 //
-// One level of Parallel-BFS (Fig. 1, lines 10-29) runs as two phases separated
+// One level of Parallel-BFS (one pass of Fig. 1's main loop) runs as two phases separated
 // by a grid-wide barrier:
 //
-//   EXPLORE  (lines 16-18)  the level's e_l edges are split into P_l chunks of
+//   EXPLORE  (Fig. 1, thread count to EXPLORE-VERTEX)  the level's e_l edges are split into P_l chunks of
 //            C_l = ceil(e_l / P_l) consecutive edges, one chunk per warp, with
-//            P_l = min(P, ceil(e_l / grain)) (line 16; grain = 1 is the paper's
+//            P_l = min(P, ceil(e_l / grain)) (Fig. 1's thread count; grain = 1 is the paper's
 //            formula).  A warp finds its start (frontier entry, edge offset) by
-//            a search on the exclusive degree scan EX (line 17), then walks its
+//            a search on the exclusive degree scan EX (Find-StartExpPoint), then walks its
 //            edges: for an edge (u, v) with level[v] == -1 it stores
 //            level[v] = l + 1 and parent[v] = u with plain (relaxed, non-RMW)
 //            stores and emits the candidate pair (v, u) into its own region of
-//            the candidate buffer (line 18; Algorithm paragraph).
-//   COMPACT  (lines 19-29)  each warp re-reads parent[v] for its candidates and
+//            the candidate buffer (EXPLORE-VERTEX; Algorithm section).
+//   COMPACT  (Fig. 1, owner check to linearisation)  each warp re-reads parent[v] for its candidates and
 //            keeps (v, u) iff parent[v] == u: the owner of v is the vertex
 //            whose store to parent[v] landed last, so exactly one candidate
-//            per newly reached v survives (lines 19-23 with the owner id taken
+//            per newly reached v survives (Fig. 1's owner check, with the owner id taken
 //            to be the parent vertex).  A single-pass decoupled look-back scan
 //            over the chunks, in chunk order, gives every survivor its slot in
-//            the next frontier (lines 24-29) and, in the same pass, the
+//            the next frontier (Sizes prefix sum, linearisation) and, in the same pass, the
 //            exclusive prefix sum of the survivors' degrees, i.e. the next
-//            level's degree gather and EdgeSum scan (lines 12-15).
+//            level's degree gather and EdgeSum scan.
 //
 // The next frontier is stored as three int32 arrays: F (vertex), RS (first CSR
 // position of its row) and EX (exclusive degree prefix, with EX[n] = e).
@@ -281,7 +281,7 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
   return x;
 }
 
-// P_l and C_l of a level (Fig. 1 line 16 with a grain; Algorithm paragraph:
+// P_l and C_l of a level (Fig. 1's thread count, with a grain; Algorithm section:
 // "(almost) equal division" of the e_l edges).  Shared by host and device.
 __host__ __device__ inline void level_sizing(int e_l, int P, int grain, int work_insensitive, int* P_l,
                                              int* C_l) {
@@ -424,7 +424,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
   const int lnext = l + 1;
   const unsigned long long pol = col_policy();
 
-  // Find-StartExpPoint (line 17): the last frontier entry i with EX[i] <=
+  // Find-StartExpPoint (Fig. 1): the last frontier entry i with EX[i] <=
   // e_begin (upper bound minus one), by a 32-ary search -- every round the
   // lanes probe 32 evenly spaced entries of [lo, hi) and keep the last probe
   // that is still <= e_begin.  Invariant: EX[lo] <= e_begin < EX[hi].
@@ -565,9 +565,9 @@ __device__ __forceinline__ int next_direction(const Params& p, int dir_l, long l
   return (n_next * p.beta < (long long)p.n && n_next < n_l) ? 0 : 1;
 }
 
-// Dedup (lines 19-23) and linearisation (lines 24-29) of the candidates of one
+// Dedup (Fig. 1, owner check) and linearisation (Sizes prefix sum) of the candidates of one
 // CTA's chunks, plus the degree gather and exclusive scan of the next frontier
-// (lines 12-15 of the next level).  Called by every thread of a CTA that holds
+// (Fig. 1's degree gather and EdgeSum of the next level).  Called by every thread of a CTA that holds
 // at least one of the level's P_l chunks; warps without a chunk pass cnt = 0.
 //
 // Pass 1 (per warp): candidates 128 at a time (S3BFS_CR per lane), all loads
@@ -1094,7 +1094,7 @@ __device__ __forceinline__ void record_level(const Params& p, int l, int n_l, in
   }
 }
 
-// a0 (Fig. 1 lines 1-8): level = parent = -1 except level[s] = 0, parent[s] =
+// a0 (Fig. 1, initialisation): level = parent = -1 except level[s] = 0, parent[s] =
 // s; F_0 = [s] with its row start and degree; clear the scan and barrier
 // state (ctas arrival words; none if 0) and the visited bits.  Grid-stride.
 __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {

@@ -69,7 +69,7 @@ def test_graph_key_classes():
 
 
 def test_skew_needs_a_large_graph():
-    # skew is judged on the 2^18 highest-degree vertices; below that every
+    # skew is measured on the 2^18 highest-degree vertices; below that every
     # vertex is covered and the class is flat
     deg = np.array([5] * 10)
     rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
