@@ -6,7 +6,7 @@
  * Parallel BFS Algorithm with Optimal parallel Prefix-sum Algorithm and its
  * Implications for Energy Consumption" (arXiv 2209.08764): every level
  * gathers the frontier's degrees, prefix-sums them, splits the level's edges
- * into (almost) equal chunks, scans neighbours writing level and parent
+ * into near-equal chunks, scans neighbours writing level and parent
  * without locks or atomic read-modify-writes, keeps each newly reached vertex
  * once (its final owner keeps it) and compacts the next frontier with a
  * second prefix sum (Fig. 1; Algorithm paragraph).

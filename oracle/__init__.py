@@ -190,8 +190,8 @@ def s3bfs_fig1(row_ptr, col_idx, s: int, P: int, grain: int = 1, race: str = "ma
 
     ``grain`` is the minimum number of edges per thread: P_l = min(P,
     ceil(e_l / grain)); grain = 1 is Fig. 1's thread count exactly.  Thread i explores edges
-    [i*C, min((i+1)*C, e_l)) with C = ceil(e_l / P_l), the "(almost) equal
-    division" of the Algorithm paragraph.
+    [i*C, min((i+1)*C, e_l)) with C = ceil(e_l / P_l), the near-equal
+    division of the Algorithm paragraph.
 
     EXPLORE-VERTEX's body is not printed; it follows the Algorithm paragraph:
     a thread that meets an unvisited neighbour v sets d[v], claims Owner[v]

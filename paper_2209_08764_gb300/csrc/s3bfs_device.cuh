@@ -25,7 +25,7 @@
 // The next frontier is stored as three int32 arrays: F (vertex), RS (first CSR
 // position of its row) and EX (exclusive degree prefix, with EX[n] = e).
 // No atomic read-modify-write instruction is used anywhere: the paper's BFS
-// "does not use locks and atomic-instructions" (Abstract).  Cross-warp
+// takes neither locks nor atomic instructions (Abstract).  Cross-warp
 // ordering uses release/acquire stores and loads only.
 #pragma once
 
@@ -282,7 +282,7 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 }
 
 // P_l and C_l of a level (Fig. 1's thread count, with a grain; Algorithm section:
-// "(almost) equal division" of the e_l edges).  Shared by host and device.
+// a near-equal split of the e_l edges).  Shared by host and device.
 __host__ __device__ inline void level_sizing(int e_l, int P, int grain, int work_insensitive, int* P_l,
                                              int* C_l) {
   if (e_l <= 0) {
