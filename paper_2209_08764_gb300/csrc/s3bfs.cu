@@ -165,9 +165,12 @@ __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, 
   // warp gw's region: 128 entries per 128-vertex group it owns
   const int gpw = ((p.nwords >> 2) + P - 1) / P;
   const long long base = (long long)gw * gpw * 128;
-  int work = 0;
-  const int total = after_bu ? ld_relaxed(p.ulist_cnt + gw) : bu_unvisited(p, gw, P, p.ulist + base);
-  const int cnt = bu_scan(p, l, fb_cur, gw, total, p.ulist + base, p.cand + base, &work);
+  int work = 0, first = 0, work0 = 0;
+  const int total = after_bu ? ld_relaxed(p.ulist_cnt + gw)
+                             : bu_unvisited(p, l, fb_cur, gw, P, p.ulist + base, p.cand + base, &first, &work0);
+  const int cnt = first + bu_scan(p, l, fb_cur, gw, total, p.ulist + base, p.cand + base + first, &work,
+                                  after_bu ? 0 : 1);
+  work += __reduce_add_sync(0xffffffffu, work0);
   if (!grid_sync(p, ++*bar)) return false;
   if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
 #if S3BFS_BU_BITMAP

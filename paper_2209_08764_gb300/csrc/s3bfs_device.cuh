@@ -993,11 +993,15 @@ __device__ __forceinline__ void bu_search(const Params& p, const uint32_t* fb, i
 // A bottom-up level that follows a top-down one starts by listing, per warp,
 // the unvisited vertices of degree > 0 among the 128-vertex groups gw, gw +
 // P, ... (level and row bounds of four 32-vertex words in flight per lane).
-// Returns the list length; the list goes to ulist (at most 128 per group).
-__device__ inline int bu_unvisited(const Params& p, int gw, int P, int* ulist) {
+// Each listed vertex first tests its first neighbour: most find their parent
+// there (the highest-degree neighbour on a renumbered graph), are written and
+// emitted at once (*found candidates to out, *work entries examined) and
+// never enter the list.  Returns the list length (at most 128 per group).
+__device__ inline int bu_unvisited(const Params& p, int l, const uint32_t* fb, int gw, int P, int* ulist, int2* out,
+                                   int* found, int* work) {
   const int lane = threadIdx.x & (kWarp - 1);
   const unsigned lt = (1u << lane) - 1u;
-  int cnt = 0;
+  int cnt = 0, nf = 0, wk = 0;
   for (int q = gw; q < (p.nwords >> 2); q += P) {
     int lv[4], rs[4], re[4];
 #pragma unroll
@@ -1008,15 +1012,36 @@ __device__ inline int bu_unvisited(const Params& p, int gw, int P, int* ulist) {
       re[j] = __shfl_down_sync(kFull, rs[j], 1);
       if (lane == kWarp - 1) re[j] = v < p.n ? __ldg(p.row_ptr + v + 1) : 0;
     }
+    bool unv[4];
+    int c0[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int v = (q << 7) + (j << 5) + lane;
-      const bool keep = v < p.n && lv[j] < 0 && re[j] > rs[j];
+      unv[j] = v < p.n && lv[j] < 0 && re[j] > rs[j];
+      c0[j] = unv[j] ? __ldg(p.col_idx + rs[j]) : -1;
+    }
+    bool hit[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hit[j] = c0[j] >= 0 && in_frontier(p, fb, l, c0[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int v = (q << 7) + (j << 5) + lane;
+      wk += unv[j] ? 1 : 0;
+      if (hit[j]) {
+        p.level[v] = l + 1;
+        p.parent[v] = c0[j];
+      }
+      const unsigned fm = __ballot_sync(kFull, hit[j]);
+      if (hit[j]) out[nf + __popc(fm & lt)] = make_int2(v, c0[j]);
+      nf += __popc(fm);
+      const bool keep = unv[j] && !hit[j];
       const unsigned km = __ballot_sync(kFull, keep);
       if (keep) ulist[cnt + __popc(km & lt)] = v;
       cnt += __popc(km);
     }
   }
+  *found = nf;
+  *work = wk;
   return cnt;
 }
 
@@ -1027,8 +1052,9 @@ __device__ inline int bu_unvisited(const Params& p, int gw, int P, int* ulist) {
 // survive the compaction's dedup); the others stay in the list, compacted in
 // place (a kept entry never lands past one not yet read).  Returns the
 // candidates written to out; *work = neighbour entries examined (warp total).
+// skip: the first entry of every row was tested already (by bu_unvisited).
 __device__ inline int bu_scan(const Params& p, int l, const uint32_t* fb, int gw, int total, int* ulist, int2* out,
-                              int* work) {
+                              int* work, int skip) {
   const int lane = threadIdx.x & (kWarp - 1);
   const unsigned lt = (1u << lane) - 1u;
   int cnt = 0, kept = 0, wk = 0;
@@ -1043,7 +1069,7 @@ __device__ inline int bu_scan(const Params& p, int l, const uint32_t* fb, int gw
     }
 #pragma unroll
     for (int s = 0; s < kBuV; ++s) {
-      k[s] = act[s] ? __ldg(p.row_ptr + v[s]) : 0;
+      k[s] = act[s] ? __ldg(p.row_ptr + v[s]) + skip : 0;
       re[s] = act[s] ? __ldg(p.row_ptr + v[s] + 1) : 0;
     }
     bool found[kBuV];
