@@ -34,7 +34,7 @@ SPACE = {
     "ctas": [0, -1],          # -1: one CTA per SM (resolved by the caller)
     "relabel": [0, -1, 1],
     "direction": [0, 1],      # tried only on symmetric graphs
-    "do_alpha": [0, 4, 60],   # bottom-up switch threshold (0 = 15)
+    "do_alpha": [0, 5, 10, 30],  # bottom-up switch threshold (0 = 15)
 }
 
 
