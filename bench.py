@@ -260,7 +260,25 @@ def cpu_baseline(w, rp, ci, srcs, budget_s):
         edges += oracle.traversed_edges(rp, level)
         k += 1
     return {"value": edges / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"first {k} of the {len(srcs)} sources, one traversal each ({t:.1f} s)"}
+            "sample": f"first {k} of the {len(srcs)} sources, one traversal each ({t:.1f} s)",
+            "host": host_info()}
+
+
+def host_info():
+    """CPU model and logical cores of the host the CPU baseline ran on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    return {"cpu": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
 
 
 def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas):
@@ -559,12 +577,13 @@ def main():
     if rank == 0 and not direction and args.with_do and w["kind"] != "grid":
         # the same sources with direction-optimising levels (bottom-up where the
         # frontier is large); the headline value stays the top-down level step
-        do = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, 1, summary=True)
+        # (rank 0 alone, without collectives: the other ranks do not run these arms)
+        do = measure_single(args, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas, 1, summary=True)
         do["speedup_vs_top_down"] = round(do["value"] / line["value"], 3)
         line["direction_optimising"] = do
     if rank == 0 and not direction and args.with_wi and not args.work_insensitive:
         # the paper's comparison arm: every warp active at every level
-        wi = measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas, 0, summary=True,
+        wi = measure_single(args, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas, 0, summary=True,
                             tuned=dict(tuned or {}, work_insensitive=1))
         wi["time_ratio_vs_work_sensitive"] = round(wi["ms_level_step_median"] / line["ms_level_step_median"], 3)
         e_ws, e_wi = (line.get("energy") or {}), (wi.get("energy") or {})
@@ -755,7 +774,9 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "harmonic_mean_gteps_level_step": float(hmean),
                 "ms_level_step_median": float(np.median(ms_loop)),
+                "ms_level_step_min": float(np.min(ms_loop)), "ms_level_step_max": float(np.max(ms_loop)),
                 "levels_median": float(np.median(recs[:, 5])),
+                "us_per_level_median": float(np.median(ms_loop * 1e3 / recs[:, 5])),
                 "ctas": info["ctas"], "warps": info["warps"]}
         if e2e:
             line["e2e"] = e2e

@@ -433,3 +433,33 @@ def test_graphs_of_different_sizes_coexist():
     finally:
         for d in devs:
             d.close()
+
+
+def test_batch_edge_sizes(rmat16):
+    rp, ci, srcs, keys = rmat16
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    g = B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, B.BFS_VALIDATE | B.BFS_SYMMETRIC, None, stream)
+    try:
+        n = len(rp) - 1
+        # k = 0 does nothing and succeeds
+        B.bfs_run_batch(g, np.zeros(1, np.int32), 0, np.zeros(1, np.int32), None, None)
+        # k = 1 through the bitmask path equals a single traversal
+        L = np.empty((1, n), np.int32)
+        Pm = np.empty((1, n), np.int32)
+        s = int(srcs[0])
+        B.bfs_run_batch(g, np.array([s], np.int32), 1, L, Pm, None)
+        want, _ = oracle.bfs(rp, ci, s)
+        assert np.array_equal(L[0], want)
+        oracle.check_bfs_tree(rp, ci, s, L[0], Pm[0], keys=keys)
+        # the same source twice in one batch: both rows are that source's traversal
+        L2 = np.empty((2, n), np.int32)
+        B.bfs_run_batch(g, np.array([s, s], np.int32), 2, L2, None, None)
+        assert np.array_equal(L2[0], want) and np.array_equal(L2[1], want)
+    finally:
+        B.bfs_destroy(g)
+
+
+def test_server_needs_graphs():
+    with pytest.raises(B.BFSError):
+        B.bfs_server_create([], None, None)
