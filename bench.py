@@ -233,7 +233,8 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": config_of(args.workload, w, rp, ci),
-            "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
