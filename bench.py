@@ -439,20 +439,27 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
     so.levels_per_launch = args.serve_levels_per_launch
     srv = B.bfs_server_create(handles, so, stream.cuda_stream)
     done = {}
-    nxt = 0
+    # a client thread submits every query at its arrival time (a submission
+    # wakes a running launch); this thread is the scheduler, polling
+    import threading
     t0 = time.perf_counter()
+
+    def client():
+        for i in range(N):
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            B.bfs_server_submit(srv, int(gsel[i]), int(srcs[i]), None, None, i)
+
+    th = threading.Thread(target=client, daemon=True)
+    th.start()
     while len(done) < N:
-        now = time.perf_counter() - t0
-        while nxt < N and arrivals[nxt] <= now:
-            B.bfs_server_submit(srv, int(gsel[nxt]), int(srcs[nxt]), None, None, nxt)
-            nxt += 1
-        q, r = B.bfs_server_pending(srv)
-        if q == 0 and r == 0:
-            if nxt < N:
-                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
-            continue
         for c in B.bfs_server_poll(srv, 256):
             done[c.tag] = c
+        q, r = B.bfs_server_pending(srv)
+        if q == 0 and r == 0 and len(done) < N:
+            time.sleep(20e-6)
+    th.join()
     makespan = time.perf_counter() - t0
     B.bfs_server_destroy(srv)
     # the library stamps completions with the host's monotonic clock, the
@@ -468,7 +475,7 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
             "config": {"workload": "serving-pool32", "graphs": [g[0] for g in graphs], "queries": N,
                        "load": load if load > 0 else "all at t=0", "lambda_qps": lam if load > 0 else None,
                        "slots": args.serve_slots, "local_levels": args.serve_local_levels,
-                       "levels_per_launch": args.serve_levels_per_launch or 8,
+                       "levels_per_launch": args.serve_levels_per_launch or 64,
                        "arrivals": "Poisson, graph uniform over the pool, source uniform over non-isolated, seed 5"},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "mean": float(lat.mean() * 1e3)},
@@ -527,7 +534,7 @@ def main():
                          "0 = every query at t = 0 (saturation throughput)")
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-levels-per-launch", type=int, default=0,
-                    help="bfs_server_opts.levels_per_launch (0 = the library default, 8)")
+                    help="bfs_server_opts.levels_per_launch (0 = the library default, 64)")
     ap.add_argument("--serve-local-levels", type=int, default=0,
                     help="bfs_server_opts.local_levels (0 = off)")
     args = ap.parse_args()

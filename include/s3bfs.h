@@ -257,9 +257,10 @@ typedef struct bfs_server bfs_server; /* opaque; owned by the library */
 typedef struct bfs_server_opts {
   int32_t slots;             /* queries running at once (<= 128 and <= the grid's CTAs);
                                 0 = 64 */
-  int32_t levels_per_launch; /* levels each launch may run before the scheduler admits
-                                new queries; 0 = 8 (a launch also ends when a query
-                                finishes) */
+  int32_t levels_per_launch; /* level steps a launch may run before the scheduler
+                                retires and admits; 0 = 64 (a launch also ends when a
+                                query finishes, and after the current step when a
+                                submission arrives) */
   int32_t chunk_edges;       /* grain, as bfs_opts.chunk_edges; 0 = 64 */
   int32_t cta_warps;         /* 8 or 32 warps per CTA; 0 = 8 */
   int32_t spin_limit_ms;     /* device wait limit; 0 = 1000 */
@@ -304,7 +305,10 @@ int bfs_server_create(bfs_graph *const *graphs, int32_t ngraphs, const bfs_serve
  * NULL to discard the result) receive the result as in bfs_run, device or
  * host pointers; they must stay valid until the query's completion is
  * returned by bfs_server_poll.  Host-side only: nothing runs until the next
- * poll.  Errors: BFS_E_INVAL.
+ * poll.  May be called from any thread, also while another thread is inside
+ * bfs_server_poll: a launch then running returns after its current level
+ * step (a host-mapped wake flag), so that the next poll admits the query.
+ * Errors: BFS_E_INVAL.
  */
 int bfs_server_submit(bfs_server *s, int32_t graph, int32_t src, int32_t *level_out, int32_t *parent_out,
                       int64_t tag);
@@ -314,8 +318,10 @@ int bfs_server_submit(bfs_server *s, int32_t graph, int32_t src, int32_t *level_
  * launch over every running query (it returns when a query finishes or after
  * levels_per_launch levels), retire the finished ones.  Up to cap completion
  * records are written to out (the rest are kept for later polls); *ndone is
- * their number.  Blocks for the launch.  Call it in a loop while queries are
- * queued or running (bfs_server_pending).
+ * their number.  Blocks for the launch, without holding the server's lock
+ * (submissions from other threads proceed meanwhile).  Call it in a loop
+ * while queries are queued or running (bfs_server_pending), from one thread
+ * at a time (a second concurrent call fails with BFS_E_INVAL).
  */
 int bfs_server_poll(bfs_server *s, bfs_completion *out, int32_t cap, int32_t *ndone);
 

@@ -111,7 +111,7 @@ struct bfs_server {
   int device = 0;
   cudaStream_t stream = nullptr;
   int sms = 0, wpc = 8, ctas = 0;
-  int nslots = 64, levels_per_launch = 8, grain = 64;
+  int nslots = 64, levels_per_launch = 64, grain = 64;
   int local_levels = 0;
   long long spin_ns = 1000000000ll;
   std::vector<bfs_graph*> graphs;
@@ -124,6 +124,9 @@ struct bfs_server {
   DevState* d_st = nullptr;        // the server's barrier / error state
   int32_t* d_arrive = nullptr;
   int32_t* d_finished = nullptr;
+  volatile int32_t* h_wake = nullptr;  // pinned, mapped: set by submissions
+  int32_t* d_wake = nullptr;           // its device address
+  bool polling = false;                // a poll is in progress (one poller at a time)
   DevState* h_st = nullptr;        // pinned
   std::vector<Query> running;      // by slot
   std::vector<bool> busy;
@@ -152,6 +155,7 @@ extern "C" void bfs_server_destroy(bfs_server* s) {
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_slots) cudaFreeHost(s->h_slots);
   if (s->h_st) cudaFreeHost(s->h_st);
+  if (s->h_wake) cudaFreeHost(const_cast<int32_t*>(s->h_wake));
   cudaSetDevice(cur);
   delete s;
 }
@@ -219,6 +223,14 @@ static int server_create_impl(bfs_server* s, bfs_graph* const* graphs, int32_t n
     cudaGetLastError();
     return fail(BFS_E_NOMEM, "pinned host allocation failed");
   }
+  int32_t* hw = nullptr;
+  if (cudaHostAlloc((void**)&hw, sizeof(int32_t) * 4, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BFS_E_NOMEM, "mapped host allocation failed");
+  }
+  s->h_wake = hw;
+  *s->h_wake = 0;
+  CUDA_TRY(cudaHostGetDevicePointer((void**)&s->d_wake, hw, 0));
   memset(s->h_slots, 0, sizeof(SlotDev) * (size_t)s->nslots);
   CUDA_TRY(cudaMemsetAsync(s->d_slots, 0, sizeof(SlotDev) * (size_t)s->nslots, s->stream));
   s->running.assign((size_t)s->nslots, Query());
@@ -265,6 +277,7 @@ extern "C" int bfs_server_submit(bfs_server* s, int32_t graph, int32_t src, int3
   q.t_submit = now_us();
   std::lock_guard<std::mutex> lock(s->mu);
   s->queue.push_back(q);
+  *s->h_wake = 1;  // a running launch returns after its current step
   return BFS_OK;
 }
 
@@ -415,7 +428,10 @@ static int retire(bfs_server* s, int slot, int status, bfs_completion* c) {
   return BFS_OK;
 }
 
-static int poll_impl(bfs_server* s) {
+// One scheduling round.  Called with s->mu held; the lock is released while
+// the launch runs on the GPU, so that other threads can submit meanwhile (a
+// submission sets the wake flag and the launch returns after its step).
+static int poll_impl(bfs_server* s, std::unique_lock<std::mutex>& lock) {
   int rc = admit(s);
   if (rc != BFS_OK) return rc;
   bool any = false;
@@ -431,10 +447,14 @@ static int poll_impl(bfs_server* s) {
   sp.local_levels = s->local_levels;
   sp.local_edges = 256 * s->wpc;
   sp.finished = s->d_finished;
+  sp.wake = s->d_wake;
   sp.st = s->d_st;
   sp.bar_arrive = s->d_arrive;
   sp.spin_ns = s->spin_ns;
   sp.debug_flags = 0;
+  // submissions from now on end the launch early; the queries still queued
+  // (no slot or no memory) wait for a query to finish, which ends it anyway
+  *s->h_wake = 0;
   CUDA_TRY(cudaMemsetAsync(s->d_st, 0, sizeof(DevState), s->stream));
   CUDA_TRY(cudaMemsetAsync(s->d_arrive, 0, sizeof(int32_t) * ((size_t)(s->ctas + 3) / 4 * 4), s->stream));
   CUDA_TRY(cudaMemsetAsync(s->d_finished, 0, sizeof(int32_t), s->stream));
@@ -444,7 +464,10 @@ static int poll_impl(bfs_server* s) {
   CUDA_TRY(cudaMemcpyAsync(s->h_slots, s->d_slots, sizeof(SlotDev) * (size_t)s->nslots, cudaMemcpyDeviceToHost,
                            s->stream));
   CUDA_TRY(cudaMemcpyAsync(s->h_st, s->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
-  CUDA_TRY(cudaStreamSynchronize(s->stream));
+  lock.unlock();
+  const cudaError_t sync_err = cudaStreamSynchronize(s->stream);
+  lock.lock();
+  CUDA_TRY(sync_err);
   const int server_err = s->h_st->err;
   std::vector<bfs_completion> fin;
   for (int i = 0; i < s->nslots; ++i) {
@@ -475,12 +498,18 @@ static int poll_impl(bfs_server* s) {
 extern "C" int bfs_server_poll(bfs_server* s, bfs_completion* out, int32_t cap, int32_t* ndone) {
   if (!s) return fail(BFS_E_INVAL, "server is NULL");
   if (ndone) *ndone = 0;
-  std::lock_guard<std::mutex> lock(s->mu);
+  std::unique_lock<std::mutex> lock(s->mu);
+  if (s->polling) return fail(BFS_E_INVAL, "bfs_server_poll called from two threads at once");
+  s->polling = true;
   int cur = 0;
-  if (cudaGetDevice(&cur) != cudaSuccess) return fail(BFS_E_CUDA, "cudaGetDevice failed");
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    s->polling = false;
+    return fail(BFS_E_CUDA, "cudaGetDevice failed");
+  }
   if (cur != s->device) cudaSetDevice(s->device);
-  const int rc = poll_impl(s);
+  const int rc = poll_impl(s, lock);
   if (cur != s->device) cudaSetDevice(cur);
+  s->polling = false;
   int k = 0;
   while (out && k < cap && !s->done.empty()) {
     out[k++] = s->done.front();

@@ -39,6 +39,9 @@ struct ServeParams {
   int32_t local_levels;
   int32_t local_edges;
   int32_t* finished;   // set when a query finished during this launch
+  // host-mapped flag: set by a submission while the launch runs, so that the
+  // launch returns after its current step and the query gets admitted
+  const volatile int32_t* wake;
   // grid barrier state of the server
   DevState* st;
   int32_t* bar_arrive;
@@ -147,8 +150,11 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
   __shared__ int s_q, s_rank, s_size;
   __shared__ long long s_w[kMaxSlots];
   const int wib = threadIdx.x >> 5;
+  const bool watch = blockIdx.x == 0 && threadIdx.x == 0 && sp.wake != nullptr;
   int bar = 0;
   for (int it = 0; it < sp.max_levels; ++it) {
+    // read early: the host-memory load overlaps the step's work
+    const int woke = watch ? *sp.wake : 0;
     serve_assign(sp, s_w, &s_q, &s_rank, &s_size);
     __syncthreads();
     const int q = s_q, rank = s_rank, gsize = s_size;
@@ -206,6 +212,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
         }
       }
     }
+    if (woke) st_relaxed(sp.finished, 1);  // a query waits: end after this step
     if (!grid_sync(sp, ++bar)) break;
     if (ld_relaxed(sp.finished) != 0) break;  // retire and admit before going on
   }

@@ -188,3 +188,52 @@ def test_bad_submissions():
         B.bfs_server_destroy(s)
         for h in handles:
             B.bfs_destroy(h)
+
+
+def test_submissions_from_another_thread_while_polling():
+    """A client thread submits while this thread polls (the poll holds no lock
+    while its launch runs; a submission wakes the launch): every result still
+    equals the oracle's."""
+    import threading
+    import time
+
+    import torch
+    pool = _pool()
+    handles = _make(pool)
+    so = B.bfs_server_opts()
+    so.levels_per_launch = 1 << 20  # only completions and wake-ups end a launch
+    s = B.bfs_server_create(handles, so, torch.cuda.current_stream().cuda_stream)
+    try:
+        rng = np.random.default_rng(3)
+        subs = []
+        for t in range(30):
+            gi = int(rng.integers(len(pool)))
+            rp = pool[gi][1]
+            subs.append((gi, int(graphgen.sample_sources(rp, 1, seed=300 + t)[0])))
+        outs = {t: np.full(len(pool[gi][1]) - 1, 5, np.int32) for t, (gi, _) in enumerate(subs)}
+
+        def client():
+            for t, (gi, src) in enumerate(subs):
+                B.bfs_server_submit(s, gi, src, outs[t], None, t)
+                time.sleep(0.0005)
+
+        th = threading.Thread(target=client)
+        th.start()
+        got = {}
+        t_end = time.time() + 120
+        while len(got) < len(subs) and time.time() < t_end:
+            for c in B.bfs_server_poll(s, 64):
+                got[c.tag] = c
+            if th.is_alive() or B.bfs_server_pending(s) != (0, 0):
+                time.sleep(0.0001)
+        th.join()
+        assert sorted(got) == list(range(len(subs)))
+        for t, (gi, src) in enumerate(subs):
+            name, rp, ci, _ = pool[gi]
+            assert got[t].status == 0
+            want, _ = oracle.bfs(rp, ci, src)
+            assert np.array_equal(outs[t], want), f"query {t} on {name}"
+    finally:
+        B.bfs_server_destroy(s)
+        for h in handles:
+            B.bfs_destroy(h)
