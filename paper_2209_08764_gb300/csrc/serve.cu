@@ -28,7 +28,14 @@
 
 using namespace s3bfs;
 
-__global__ void __launch_bounds__(256) k_serve_init(Params p) { init_traversal(p, 0); }
+// a0 for one query, and the slot's copy of its level-0 sizes
+__global__ void __launch_bounds__(256) k_serve_init(Params p, SlotDev* sd) {
+  init_traversal(p, 0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sd->n = 1;
+    sd->e = p.row_ptr[p.src + 1] - p.row_ptr[p.src];
+  }
+}
 
 __global__ void __launch_bounds__(256) k_serve_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
                                                         const int32_t* level, const int32_t* parent,
@@ -380,7 +387,7 @@ static int admit(bfs_server* s) {
     sd.active = 1;
     CUDA_TRY(cudaMemcpyAsync(s->d_slots + slot, &sd, sizeof(SlotDev), cudaMemcpyHostToDevice, s->stream));
     const int grid = std::max(1, std::min(s->sms * 8, (int)((n / 4 + 255) / 256)));
-    k_serve_init<<<grid, 256, 0, s->stream>>>(p);
+    k_serve_init<<<grid, 256, 0, s->stream>>>(p, s->d_slots + slot);
     CUDA_TRY(cudaGetLastError());
     q.t_admit = now_us();
     s->running[(size_t)slot] = q;

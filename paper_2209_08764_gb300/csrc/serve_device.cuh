@@ -26,6 +26,8 @@ struct SlotDev {
   int32_t active;      // 1 while it runs, 0 when done (or failed)
   int32_t num_levels;  // levels done
   int32_t pad;
+  int32_t n, e;        // frontier size and edge count of the current level (copies of the
+                       // query's control block, read by every CTA at every step in one load)
   long long reached, edges, cands;
 };
 
@@ -59,13 +61,10 @@ __device__ __forceinline__ void serve_assign(const ServeParams& sp, long long* s
   const int t = threadIdx.x;
   if (t < sp.nslots) {
     const SlotDev& sd = sp.slots[t];
-    long long w = 0;
-    if (ld_relaxed(&sd.active)) {
-      const int l = ld_relaxed(&sd.level);
-      const int n = ld_relaxed(&sd.p.st->ctrl[l & 1].n);
-      if (n > 0) w = max(ld_relaxed(&sd.p.st->ctrl[l & 1].e), 1);
-    }
-    s_w[t] = w;
+    const int act = ld_relaxed(&sd.active);
+    const int n = ld_relaxed(&sd.n);
+    const int e = ld_relaxed(&sd.e);
+    s_w[t] = act && n > 0 ? (long long)max(e, 1) : 0ll;
   }
   __syncthreads();
   if (t == 0) {
@@ -105,8 +104,8 @@ __device__ void serve_local(const ServeParams& sp, SlotDev* sd) {
   for (int k = 0; k < sp.local_levels; ++k) {
     const int l = ld_relaxed(&sd->level);
     const int par = l & 1;
-    const int n_l = ld_relaxed(&p.st->ctrl[par].n);
-    const int e_l = ld_relaxed(&p.st->ctrl[par].e);
+    const int n_l = ld_relaxed(&sd->n);
+    const int e_l = ld_relaxed(&sd->e);
     if (n_l <= 0 || e_l > sp.local_edges) break;  // uniform: every thread read the same words
     int P_l, C_l;
     level_sizing(e_l, W, sp.grain, 0, &P_l, &C_l);
@@ -131,6 +130,8 @@ __device__ void serve_local(const ServeParams& sp, SlotDev* sd) {
       sd->edges += e_l;
       sd->cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
       sd->num_levels = l + 1;
+      st_relaxed(&sd->n, n_next);
+      st_relaxed(&sd->e, ld_relaxed(&p.st->ctrl[par ^ 1].e));
       st_relaxed(&sd->level, l + 1);
       const bool done = n_next <= 0 || ld_relaxed(&p.st->err) != 0;
       if (done) {
@@ -163,10 +164,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
     SlotDev* sd = q >= 0 ? sp.slots + q : nullptr;
     // a query alone on this CTA with a small level: several levels now, alone
     bool local = false;
-    if (sd && gsize == 1 && sp.local_levels > 0) {
-      const int l0 = ld_relaxed(&sd->level);
-      local = ld_relaxed(&sd->p.st->ctrl[l0 & 1].e) <= sp.local_edges;
-    }
+    if (sd && gsize == 1 && sp.local_levels > 0) local = ld_relaxed(&sd->e) <= sp.local_edges;
     if (local) {
       serve_local<W>(sp, sd);
       sd = nullptr;  // nothing left for this step's shared phases
@@ -176,8 +174,8 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
       const Params& p = sd->p;
       l = ld_relaxed(&sd->level);
       par = l & 1;
-      n_l = ld_relaxed(&p.st->ctrl[par].n);
-      e_l = ld_relaxed(&p.st->ctrl[par].e);
+      n_l = ld_relaxed(&sd->n);
+      e_l = ld_relaxed(&sd->e);
       level_sizing(e_l, gsize * W, sp.grain, 0, &P_l, &C_l);
       const int gw = rank * W + wib;
       if (gw < P_l) {
@@ -205,6 +203,8 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
         sd->edges += e_l;
         sd->cands += ld_relaxed(&p.st->ctrl[par ^ 1].c);
         sd->num_levels = l + 1;
+        st_relaxed(&sd->n, n_next);
+        st_relaxed(&sd->e, ld_relaxed(&p.st->ctrl[par ^ 1].e));
         st_relaxed(&sd->level, l + 1);
         if (n_next <= 0 || ld_relaxed(&p.st->err) != 0) {
           st_relaxed(&sd->active, 0);
