@@ -87,8 +87,8 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per launch of the level-loop kernel from the committed ncu
+def profiled(workload, key="dram_bytes_per_launch"):
+    """A per-launch counter of the level-loop kernel from the committed ncu
     summary, if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", f"level_loop_{workload}.json")
     try:
@@ -98,7 +98,39 @@ def profiled_traffic(workload):
         return None
     if p.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return p.get("dram_bytes_per_launch")
+    return p.get(key)
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the level-loop kernel (ncu), or None."""
+    return profiled(workload, "dram_bytes_per_launch")
+
+
+def gather_peak(torch, dev):
+    """Measured rate of isolated 4-byte loads at random addresses: torch's
+    gather kernel reading an int32 table of 16 MiB (L2-resident, like the
+    level array the explore tests) and of 1 GiB (HBM), with 2^27 random
+    indices each; the higher rate, in loads (sectors) per second.  This is
+    the ceiling of a kernel whose every test is one scattered load."""
+    best = 0.0
+    g = torch.Generator(device=dev).manual_seed(7)
+    out = torch.empty(1 << 27, dtype=torch.int32, device=dev)
+    for size in (1 << 22, 1 << 28):
+        table = torch.zeros(size, dtype=torch.int32, device=dev)
+        idx = torch.randint(0, size, (1 << 27,), generator=g, device=dev, dtype=torch.int64)
+        for _ in range(3):
+            torch.index_select(table, 0, idx, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            torch.index_select(table, 0, idx, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 10 * idx.numel() / (e0.elapsed_time(e1) / 1e3))
+        del table, idx
+    del out
+    return best
 
 
 class ClockSampler:
@@ -726,6 +758,15 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_level_loop", "algorithmic_bytes_per_launch": float(bytes_loop.mean()),
                 "avg_launch_ms": float(ms_loop.mean())}
+    sectors = profiled(args.workload, "l1_global_load_sectors_per_launch") if not direction else None
+    if sectors and not summary and rank == 0:
+        # the bound the explore actually meets: scattered loads, one L1 sector each
+        peak_ld = gather_peak(torch, dev)
+        ach = sectors / (ms_loop.mean() / 1e3)
+        roofline["scattered_loads"] = {"bound": "l1_scattered_sectors", "achieved": ach, "peak": peak_ld,
+                                       "unit": "sectors/s", "frac": round(ach / peak_ld, 4),
+                                       "sectors_per_launch": sectors,
+                                       "peak_kind": "measured: torch index_select of random int32"}
     hmean = len(ms_loop) / np.sum(ms_loop / 1e3 / np.tile(teps_edges, args.steps)) / 1e9
     launches = int(recs[:, 7].sum())
     energy = None
