@@ -549,6 +549,7 @@ def main():
                     help="choose the options by the autotuner (coordinate descent on 4 of the sources)")
     ap.add_argument("--tune-cache", default="", help="JSON cache file of the autotuner")
     ap.add_argument("--do-alpha", type=int, default=0, help="bfs_opts.do_alpha (0 = 15)")
+    ap.add_argument("--do-gamma", type=int, default=0, help="bfs_opts.do_gamma (0 = 2, -1 = off)")
     ap.add_argument("--do-beta", type=int, default=0, help="bfs_opts.do_beta (0 = 18)")
     ap.add_argument("--with-wi", type=int, default=1,
                     help="1 (default): add the work-insensitive arm (every warp at every level) to the line")
@@ -680,6 +681,7 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     opts.cta_warps = args.cta_warps
     opts.direction = direction
     opts.do_alpha = args.do_alpha
+    opts.do_gamma = args.do_gamma
     opts.do_beta = args.do_beta
     for k, v in (tuned or {}).items():
         setattr(opts, k, int(v))

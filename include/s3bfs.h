@@ -93,6 +93,11 @@ typedef struct bfs_opts {
                                only: with persistent = -1 every level is top-down */
   int32_t do_alpha;         /* 0 = 15 */
   int32_t do_beta;          /* 0 = 18 */
+  int32_t do_gamma;         /* a top-down level turns bottom-up only if, besides the
+                               alpha test, its frontier's edges exceed do_gamma times
+                               the unvisited vertices of degree > 0 (on a GPU a
+                               bottom-up test costs about what a top-down one does);
+                               0 = 2, -1 = no such test (Beamer's rule alone) */
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */

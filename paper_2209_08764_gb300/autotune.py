@@ -35,6 +35,7 @@ SPACE = {
     "relabel": [0, -1, 1],
     "direction": [0, 1],      # tried only on symmetric graphs
     "do_alpha": [0, 5, 10, 30],  # bottom-up switch threshold (0 = 15)
+    "do_gamma": [0, -1, 8],      # unvisited-vertex test of the switch (0 = 2, -1 = off)
 }
 
 
@@ -169,6 +170,7 @@ def tune(B, rp, ci, sources, cache_path=None, symmetric=True, flags=0, space=Non
     if not symmetric:
         sp.pop("direction", None)
         sp.pop("do_alpha", None)
+        sp.pop("do_gamma", None)
     best, best_ms, trials = coordinate_descent(make_measure(B, rp, ci, sources, flags, stream, sms, reps), sp)
     cache.put(key, best, best_ms, [[o, ms] for o, ms in trials])
     return best, key, {"cached": False, "ms": best_ms, "trials": len(trials)}

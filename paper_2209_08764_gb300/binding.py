@@ -50,6 +50,7 @@ class bfs_opts(ctypes.Structure):
         ("direction", ctypes.c_int32),
         ("do_alpha", ctypes.c_int32),
         ("do_beta", ctypes.c_int32),
+        ("do_gamma", ctypes.c_int32),
     ]
 
 

@@ -31,7 +31,8 @@ struct bfs_graph {
   int small_edges = -1;  // resolved at create: 256 edges per warp of one CTA
   int launches = 0;      // kernels launched by the current call
   int direction = 0;     // 1: direction-optimising (bottom-up levels)
-  int alpha = 15, beta = 18;
+  int alpha = 15, beta = 18, gamma = 2;
+  int32_t n_live = 0;    // vertices of degree > 0
   int32_t nwords = 0;    // words of a frontier bitmap
   uint32_t* d_fb[2] = {nullptr, nullptr};
   int32_t *d_ulist = nullptr, *d_ulist_cnt = nullptr;  // bottom-up: unvisited vertices per warp

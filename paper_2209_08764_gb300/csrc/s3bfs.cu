@@ -106,7 +106,7 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
   if (P_l == 0) {
     if (gw == 0 && lane == 0) {
       publish_empty_next(p, par);
-      if (!GRID) *s_ctrl = LevelCtrl{0, 0, 0, s_ctrl->cum, 0, 0, 0, 0};
+      if (!GRID) *s_ctrl = LevelCtrl{0, 0, 0, s_ctrl->cum, 0, 0, 0, s_ctrl->vcum};
     }
   } else if (!GRID || (int)blockIdx.x * W < P_l) {
     compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0, work,
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 8 ? 4 : 1) k_level_loop(Params
       // a streak starts: its control blocks live in shared memory
       if (threadIdx.x == 0) {
         const LevelCtrl* c = &p.st->ctrl[l & 1];
-        s_ctrl = LevelCtrl{n_l, e_l, 0, ld_relaxed(&c->cum), 0, 0, 0, 0};
+        s_ctrl = LevelCtrl{n_l, e_l, 0, ld_relaxed(&c->cum), 0, 0, 0, ld_relaxed(&c->vcum)};
       }
       __syncthreads();
     }
@@ -410,6 +410,9 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     if (opts->do_alpha < 0 || opts->do_beta < 0) return fail(BFS_E_INVAL, "do_alpha / do_beta must be >= 0");
     if (opts->do_alpha > 0) g->alpha = opts->do_alpha;
     if (opts->do_beta > 0) g->beta = opts->do_beta;
+    if (opts->do_gamma < -1) return fail(BFS_E_INVAL, "do_gamma = %d: use -1 (off), 0 (default) or > 0", opts->do_gamma);
+    if (opts->do_gamma > 0) g->gamma = opts->do_gamma;
+    if (opts->do_gamma == -1) g->gamma = 0;
   }
   if (g->direction && !(flags & BFS_SYMMETRIC))
     return fail(BFS_E_INVAL, "direction-optimising levels need a symmetric graph (BFS_SYMMETRIC)");
@@ -503,6 +506,19 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     }
   }
   const bool upload_from_host = csr_on_host;
+  if (g->direction) {
+    // vertices of degree > 0: the ones a bottom-up level can find
+    std::vector<int32_t> rp_copy;
+    const int32_t* rpp = rp;
+    if (!csr_on_host) {
+      rp_copy.resize((size_t)n + 1);
+      CUDA_TRY(cudaMemcpy(rp_copy.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+      rpp = rp_copy.data();
+    }
+    int32_t live = 0;
+    for (int32_t v = 0; v < n; ++v) live += rpp[v + 1] > rpp[v];
+    g->n_live = live;
+  }
   g->n = n;
   g->nnz = nnz;
   const size_t nnz_pad = ((size_t)nnz + 3) / 4 * 4 + 4;
@@ -656,6 +672,8 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.direction = g->persistent ? g->direction : 0;
   p.alpha = g->alpha;
   p.beta = g->beta;
+  p.gamma = g->gamma;
+  p.n_live = g->n_live;
   return p;
 }
 

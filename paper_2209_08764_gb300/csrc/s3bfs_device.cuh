@@ -96,7 +96,7 @@ struct LevelCtrl {
   int32_t dir;   // how this level runs: 0 top-down, 1 bottom-up
   int32_t fb;    // 1: the level before wrote this level's frontier bitmap
   int32_t w;     // neighbour entries the level before examined
-  int32_t pad;
+  int32_t vcum;  // n summed over this level and all earlier ones (vertices visited)
 };
 
 // Device-resident control block of one traversal.
@@ -154,7 +154,8 @@ struct Params {
   int32_t* ulist;
   int32_t* ulist_cnt;
   int32_t direction;  // 0: every level top-down; 1: direction-optimising
-  int32_t alpha, beta;
+  int32_t alpha, beta, gamma;
+  int32_t n_live;     // vertices of degree > 0 (the ones a bottom-up level can find)
 };
 
 // ---------------------------------------------------------------------------
@@ -555,13 +556,17 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
 // Asanovic and Patterson, SC 2012; the paper's conclusion names bottom-up
 // steps as compatible with S3BFS).  With m_u = nnz - cum, the degree sum of
 // the vertices still unvisited once the next frontier is known: a top-down
-// traversal turns bottom-up when the next frontier's edges exceed m_u / alpha;
-// a bottom-up one turns back when the frontier shrinks below n / beta.
+// traversal turns bottom-up when the next frontier's edges exceed m_u / alpha
+// -- and, on a GPU where a bottom-up test costs about what a top-down one
+// does, also gamma times the unvisited vertices of degree > 0 (each of which
+// a bottom-up level visits; gamma = 0 drops this test); a bottom-up one
+// turns back when the frontier shrinks below n / beta.
 __device__ __forceinline__ int next_direction(const Params& p, int dir_l, long long n_l, long long n_next,
-                                              long long e_next, long long cum) {
+                                              long long e_next, long long cum, long long vcum) {
   if (!p.direction || n_next <= 0) return 0;
   const long long m_u = (long long)p.nnz - cum;
-  if (dir_l == 0) return e_next * p.alpha > m_u ? 1 : 0;
+  const long long n_u = (long long)p.n_live - vcum;
+  if (dir_l == 0) return (e_next * p.alpha > m_u && e_next > (long long)p.gamma * n_u) ? 1 : 0;
   return (n_next * p.beta < (long long)p.n && n_next < n_l) ? 0 : 1;
 }
 
@@ -777,15 +782,17 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
     }
     const LevelCtrl cur = s_next ? *s_next : LevelCtrl{ld_relaxed(&p.st->ctrl[par].n), 0, 0,
                                                          ld_relaxed(&p.st->ctrl[par].cum),
-                                                         ld_relaxed(&p.st->ctrl[par].dir), 0, 0, 0};
+                                                         ld_relaxed(&p.st->ctrl[par].dir), 0, 0,
+                                                         ld_relaxed(&p.st->ctrl[par].vcum)};
     const long long cum = (long long)cur.cum + e_next;
+    const long long vcum = (long long)cur.vcum + n_next;
     if (n_next > p.n || e_next > p.nnz || e_next < 0 || cum > p.nnz) {
       set_err(p, BFS_E_MULTIGRAPH, 4);
       if (s_next) s_next->n = -1;
     } else {
       EXn[n_next] = (int)e_next;
       const int dir_l = cur.dir;
-      const int dir_next = next_direction(p, dir_l, cur.n, n_next, e_next, cum);
+      const int dir_next = next_direction(p, dir_l, cur.n, n_next, e_next, cum, vcum);
       LevelCtrl* c = &p.st->ctrl[np];
       st_relaxed(&c->n, (int)n_next);
       st_relaxed(&c->e, (int)e_next);
@@ -794,7 +801,9 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
       st_relaxed(&c->dir, dir_next);
       st_relaxed(&c->fb, dir_l);
       st_relaxed(&c->w, (int)w_l);
-      if (s_next) *s_next = LevelCtrl{(int)n_next, (int)e_next, (int)c_l, (int)cum, dir_next, dir_l, (int)w_l, 0};
+      st_relaxed(&c->vcum, (int)vcum);
+      if (s_next)
+        *s_next = LevelCtrl{(int)n_next, (int)e_next, (int)c_l, (int)cum, dir_next, dir_l, (int)w_l, (int)vcum};
       if (l < p.lvl_cap) {
         p.lvl[(long long)l * kLevelFields + 2] = (int)c_l;
         p.lvl[(long long)l * kLevelFields + 8] = (int)w_l;
@@ -1165,7 +1174,7 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
     p.EX[0][0] = 0;
     p.EX[0][1] = deg;
     DevState* st = p.st;
-    LevelCtrl c0 = {1, deg, 0, deg, 0, 0, 0, 0};
+    LevelCtrl c0 = {1, deg, 0, deg, 0, 0, 0, 1};
     LevelCtrl c1 = {0, 0, 0, 0, 0, 0, 0, 0};
     st->ctrl[0] = c0;
     st->ctrl[1] = c1;

@@ -26,10 +26,13 @@ class Dev:
         self.direction = opts.get("direction", 0) if self.persistent else 0
         self.alpha = opts.get("do_alpha", 0) or 15
         self.beta = opts.get("do_beta", 0) or 18
+        g = opts.get("do_gamma", 0)
+        self.gamma = 2 if g == 0 else (0 if g == -1 else g)
         self.torch = torch
         self.rp = np.ascontiguousarray(rp, np.int32)
         self.ci = np.ascontiguousarray(ci, np.int32)
         self.n = len(self.rp) - 1
+        self.n_live = int((np.diff(self.rp) > 0).sum())
         self.g = B.bfs_create_csr(self.n, len(self.ci), self.rp, self.ci if len(self.ci) else None, flags,
                                   make_opts(**opts) if opts else None, torch.cuda.current_stream().cuda_stream)
         self.info = B.bfs_graph_info(self.g)
@@ -60,21 +63,25 @@ class Dev:
         self.g = None
 
 
-def expected_directions(n, nnz, n_l, e_l, direction, alpha, beta):
+def expected_directions(n, nnz, n_l, e_l, direction, alpha, beta, gamma=0, n_live=0):
     """Direction of every level (0 top-down, 1 bottom-up) by the switching
     rule of a direction-optimising traversal (Beamer et al., SC 2012), from
     the oracle's level profile: with m_u = nnz - (e summed over the levels up
     to the next one), turn bottom-up when the next frontier's edges exceed
-    m_u / alpha; turn back when it shrinks below n / beta."""
+    m_u / alpha and gamma times the unvisited vertices of degree > 0 (n_live
+    minus the vertices of the levels up to the next one); turn back when the
+    frontier shrinks below n / beta."""
     d = [0]
     cum = int(e_l[0])
+    vcum = int(n_l[0])
     for l in range(len(n_l) - 1):
         n_next, e_next = int(n_l[l + 1]), int(e_l[l + 1])
         cum += e_next
+        vcum += n_next
         if not direction or n_next <= 0:
             nd = 0
         elif d[-1] == 0:
-            nd = 1 if e_next * alpha > nnz - cum else 0
+            nd = 1 if (e_next * alpha > nnz - cum and e_next > gamma * (n_live - vcum)) else 0
         else:
             nd = 0 if (n_next * beta < n and n_next < int(n_l[l])) else 1
         d.append(nd)
@@ -95,7 +102,8 @@ def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=64
     assert st.num_levels == len(n_l)
     assert st.reached == int(n_l.sum())
     assert st.edges_scanned == int(e_l.sum())
-    dirs = expected_directions(dev.n, len(dev.ci), n_l, e_l, dev.direction, dev.alpha, dev.beta)
+    dirs = expected_directions(dev.n, len(dev.ci), n_l, e_l, dev.direction, dev.alpha, dev.beta, dev.gamma,
+                               dev.n_live)
     bu = dirs == 1
     if not bu.any():
         assert st.work_edges == st.edges_scanned

@@ -55,3 +55,19 @@ def test_rule_by_hand_on_a_small_profile():
     # level 3: bottom-up; 20 * 10 = 200 < 100?  no -> stays 1
     # level 4: 5 * 10 = 50 < 100 and 5 < 20 -> 0
     assert d.tolist() == [0, 0, 1, 1, 0]
+
+
+def test_gamma_keeps_a_sparse_frontier_top_down():
+    # Erdős–Rényi: a level with a small frontier among many unvisited vertices
+    # passes Beamer's alpha test but not the unvisited-vertex test, and stays
+    # top-down; the dense middle level still turns bottom-up
+    rp, ci = graphgen.erdos_renyi(1 << 14, 1 << 17, seed=4)
+    s = int(graphgen.sample_sources(rp, 1, seed=2)[0])
+    n_l, e_l = _profile(rp, ci, s)
+    n = len(rp) - 1
+    live = int((np.diff(rp) > 0).sum())
+    beamer = expected_directions(n, len(ci), n_l, e_l, 1, 15, 18, gamma=0, n_live=live)
+    gpu = expected_directions(n, len(ci), n_l, e_l, 1, 15, 18, gamma=2, n_live=live)
+    assert gpu.sum() <= beamer.sum() and gpu.max() == 1
+    first_b, first_g = int(np.argmax(beamer)), int(np.argmax(gpu))
+    assert first_g >= first_b

@@ -55,16 +55,18 @@ def test_rmat16_direction_optimising(rmat16, relabel):
 
 
 @pytest.mark.parametrize("opts", [
-    dict(do_alpha=1 << 20),                    # bottom-up at almost every level
-    dict(do_alpha=1 << 20, do_beta=1),         # and never back
+    dict(do_alpha=1 << 20, do_gamma=-1),                    # bottom-up at almost every level
+    dict(do_alpha=1 << 20, do_gamma=-1, do_beta=1),         # and never back
     dict(do_alpha=2, do_beta=1 << 20),         # late switch, early switch back
-    dict(do_alpha=1 << 20, cta_warps=8),
-    dict(do_alpha=1 << 20, cta_warps=16),
-    dict(do_alpha=1 << 20, cta_warps=24),
-    dict(do_alpha=1 << 20, ctas=3),            # few warps: many words per warp
-    dict(do_alpha=1 << 20, ctas=1, cta_warps=8),
-    dict(do_alpha=1 << 20, small_level_edges=-1),
-    dict(do_alpha=1 << 20, relabel=1),
+    dict(do_gamma=-1),                         # Beamer's rule alone
+    dict(do_gamma=8),
+    dict(do_alpha=1 << 20, do_gamma=-1, cta_warps=8),
+    dict(do_alpha=1 << 20, do_gamma=-1, cta_warps=16),
+    dict(do_alpha=1 << 20, do_gamma=-1, cta_warps=24),
+    dict(do_alpha=1 << 20, do_gamma=-1, ctas=3),            # few warps: many words per warp
+    dict(do_alpha=1 << 20, do_gamma=-1, ctas=1, cta_warps=8),
+    dict(do_alpha=1 << 20, do_gamma=-1, small_level_edges=-1),
+    dict(do_alpha=1 << 20, do_gamma=-1, relabel=1),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_rmat16_forced_bottom_up(rmat16, opts):
     rp, ci, orc = rmat16
@@ -93,7 +95,7 @@ def _named():
 @pytest.mark.parametrize("name", sorted(_named()))
 def test_named_graphs_direction_optimising(name, alpha):
     rp, ci = _named()[name]
-    d = Dev(rp, ci, flags=SYM, direction=1, do_alpha=alpha)
+    d = Dev(rp, ci, flags=SYM, direction=1, do_alpha=alpha, do_gamma=-1 if alpha else 0)
     try:
         n = len(rp) - 1
         for s in sorted({0, n // 2, n - 1}):
@@ -106,7 +108,8 @@ def test_host_outputs_and_batch(rmat16):
     rp, ci, orc = rmat16
     import torch
     stream = torch.cuda.current_stream().cuda_stream
-    g = B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, SYM, B.bfs_opts(direction=1, do_alpha=1 << 20, batch_bitmask=-1),
+    g = B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, SYM,
+                         B.bfs_opts(direction=1, do_alpha=1 << 20, do_gamma=-1, batch_bitmask=-1),
                          stream)
     try:
         n = len(rp) - 1
@@ -140,6 +143,8 @@ def test_requires_symmetric_and_valid_options(rmat16):
         B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, SYM, B.bfs_opts(direction=2), stream)
     with pytest.raises(B.BFSError):
         B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, SYM, B.bfs_opts(direction=1, do_alpha=-1), stream)
+    with pytest.raises(B.BFSError):
+        B.bfs_create_csr(len(rp) - 1, len(ci), rp, ci, SYM, B.bfs_opts(direction=1, do_gamma=-2), stream)
 
 
 def test_launch_per_phase_stays_top_down(rmat16):
