@@ -156,3 +156,31 @@ def test_launch_per_phase_stays_top_down(rmat16):
             assert (pl[:, 7] == 0).all()
     finally:
         d.close()
+
+
+@pytest.mark.parametrize("flags", [B.BFS_DEVICE_PTRS | B.BFS_SYMMETRIC,
+                                   B.BFS_DEVICE_PTRS | B.BFS_SYMMETRIC | B.BFS_VALIDATE,
+                                   B.BFS_SYMMETRIC | B.BFS_DEDUP])
+def test_device_csr_and_dedup_inputs(flags):
+    # the CSR given as device pointers (the live-vertex count is then read back
+    # from the device), or cleaned by BFS_DEDUP on the host
+    import torch
+    rp, ci = graphgen.rmat(12, 16, seed=3)
+    if flags & B.BFS_DEVICE_PTRS:
+        a, b = torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda()
+    else:
+        a, b = rp, ci
+    g = B.bfs_create_csr(len(rp) - 1, len(ci), a, b, flags, B.bfs_opts(direction=1),
+                         torch.cuda.current_stream().cuda_stream)
+    try:
+        lv = torch.empty(len(rp) - 1, dtype=torch.int32, device="cuda")
+        pa = torch.empty_like(lv)
+        for s in graphgen.sample_sources(rp, 3, seed=11):
+            st = B.bfs_stats()
+            B.bfs_run(g, int(s), lv, pa, st)
+            want, _ = oracle.bfs(rp, ci, int(s))
+            assert np.array_equal(lv.cpu().numpy(), want)
+            oracle.check_bfs_tree(rp, ci, int(s), want, pa.cpu().numpy())
+            assert st.work_edges <= st.edges_scanned
+    finally:
+        B.bfs_destroy(g)
