@@ -54,18 +54,24 @@ struct ServeParams {
 // Split of gridDim.x CTAs among the running queries: every query with a
 // non-empty frontier gets one CTA plus a share of the rest proportional to
 // its level's edge count.  Whole CTA (the slot states are read in parallel,
-// one thread per slot); thread 0 then sets q (-1: idle CTA, -2: nothing
-// runs), the CTA's rank in its query's group and the group size.
-__device__ __forceinline__ void serve_assign(const ServeParams& sp, long long* s_w, int* q_out, int* rank_out,
-                                             int* size_out) {
+// one thread per slot, and kept in shared memory: s_lne[q] = level, n, e of
+// query q); thread 0 then sets q (-1: idle CTA, -2: nothing runs -- also
+// when the step before asked the launch to end), the CTA's rank in its
+// query's group and the group size.
+__device__ __forceinline__ void serve_assign(const ServeParams& sp, long long* s_w, int3* s_lne, int* q_out,
+                                             int* rank_out, int* size_out, bool check_finished) {
   const int t = threadIdx.x;
+  __shared__ int s_stop;
   if (t < sp.nslots) {
     const SlotDev& sd = sp.slots[t];
     const int act = ld_relaxed(&sd.active);
+    const int lv = ld_relaxed(&sd.level);
     const int n = ld_relaxed(&sd.n);
     const int e = ld_relaxed(&sd.e);
     s_w[t] = act && n > 0 ? (long long)max(e, 1) : 0ll;
+    s_lne[t] = make_int3(lv, n, e);
   }
+  if (t == kMaxSlots - 1) s_stop = check_finished ? ld_relaxed(sp.finished) : 0;
   __syncthreads();
   if (t == 0) {
     const int G = gridDim.x;
@@ -75,10 +81,10 @@ __device__ __forceinline__ void serve_assign(const ServeParams& sp, long long* s
       wsum += s_w[q];
       A += s_w[q] > 0;
     }
-    *q_out = A == 0 ? -2 : -1;
+    *q_out = (A == 0 || s_stop != 0) ? -2 : -1;
     const long long spare = G > A ? G - A : 0;
     int start = 0;
-    for (int q = 0; q < sp.nslots && A > 0; ++q) {
+    for (int q = 0; q < sp.nslots && A > 0 && s_stop == 0; ++q) {
       if (s_w[q] == 0) continue;
       const int g = 1 + (int)(spare * s_w[q] / wsum);
       if ((int)blockIdx.x >= start && (int)blockIdx.x < start + g) {
@@ -150,13 +156,15 @@ template <int W>
 __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParams sp) {
   __shared__ int s_q, s_rank, s_size;
   __shared__ long long s_w[kMaxSlots];
+  __shared__ int3 s_lne[kMaxSlots];
   const int wib = threadIdx.x >> 5;
   const bool watch = blockIdx.x == 0 && threadIdx.x == 0 && sp.wake != nullptr;
   int bar = 0;
   for (int it = 0; it < sp.max_levels; ++it) {
     // read early: the host-memory load overlaps the step's work
     const int woke = watch ? *sp.wake : 0;
-    serve_assign(sp, s_w, &s_q, &s_rank, &s_size);
+    // the finished flag of the step before is read with the slot states
+    serve_assign(sp, s_w, s_lne, &s_q, &s_rank, &s_size, it > 0);
     __syncthreads();
     const int q = s_q, rank = s_rank, gsize = s_size;
     __syncthreads();
@@ -172,10 +180,10 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
     int l = 0, par = 0, n_l = 0, e_l = 0, P_l = 0, C_l = 0, cnt = 0, e_begin = 0, work = 0;
     if (sd) {
       const Params& p = sd->p;
-      l = ld_relaxed(&sd->level);
+      l = s_lne[q].x;
       par = l & 1;
-      n_l = ld_relaxed(&sd->n);
-      e_l = ld_relaxed(&sd->e);
+      n_l = s_lne[q].y;
+      e_l = s_lne[q].z;
       level_sizing(e_l, gsize * W, sp.grain, 0, &P_l, &C_l);
       const int gw = rank * W + wib;
       if (gw < P_l) {
@@ -214,7 +222,8 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
     }
     if (woke) st_relaxed(sp.finished, 1);  // a query waits: end after this step
     if (!grid_sync(sp, ++bar)) break;
-    if (ld_relaxed(sp.finished) != 0) break;  // retire and admit before going on
+    // a finished query or a waiting one ends the launch at the next step's
+    // assignment (retire and admit before going on)
   }
 }
 
