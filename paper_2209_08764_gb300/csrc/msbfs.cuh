@@ -104,6 +104,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
   const int* rp = p.row_ptr;
   const int* ci = p.col_idx;
   int l = 0, bar = 0;
+  // sources with a non-empty frontier at this level: the only bits a vertex
+  // can gain now.  A vertex stops pulling once it holds all of them (and
+  // skips its row when it already did), the early exit of multi-source BFS.
+  unsigned long long active = full;
   while (true) {
     const int par = l & 1;
     const unsigned long long* cur = par ? p.fr[1] : p.fr[0];
@@ -118,11 +122,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
       if (mine) {
         const int b = __ldg(rp + v), e = __ldg(rp + v + 1);
         const unsigned long long s = p.seen[v];
-        if (s != full) {
+        const unsigned long long need = active & ~s;
+        if (need) {
           unsigned long long acc = 0;
           const int V = out_id(p, (int)v);
-          my_edges += e - b;
-          for (int j = b; j < e; j += kMsUnroll) {
+          for (int j = b; j < e && (acc & need) != need; j += kMsUnroll) {
+            my_edges += min(kMsUnroll, e - j);
             int uu[kMsUnroll];
             unsigned long long ff[kMsUnroll];
 #pragma unroll
@@ -161,12 +166,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
       const int v = __ldg(p.heavy + h);
       const int b = __ldg(rp + v), e = __ldg(rp + v + 1);
       const unsigned long long s = p.seen[v];
+      const unsigned long long need = active & ~s;
       unsigned long long nw = 0;
-      if (s != full) {
+      if (need) {
         const int V = out_id(p, v);
         unsigned long long acc = 0;
-        if (lane == 0) my_edges += e - b;
-        for (int base = b; base < e; base += kWarp) {
+        for (int base = b; base < e && (acc & need) != need; base += kWarp) {  // acc is warp-uniform
+          if (lane == 0) my_edges += min(kWarp, e - base);
           const int j = base + lane;
           int u = 0;
           unsigned long long f = 0;
@@ -197,10 +203,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
       const int v = __ldg(p.huge + h);
       const int b = __ldg(rp + v), e = __ldg(rp + v + 1);
       const unsigned long long s = p.seen[v];
+      const unsigned long long need = active & ~s;
       unsigned long long acc = 0;
-      if (s != full) {
+      if (need) {
         const int V = out_id(p, v);
-        for (int base = b + wib * kWarp; base < e; base += kWarpsPerCta * kWarp) {
+        for (int base = b + wib * kWarp; base < e && (acc & need) != need; base += kWarpsPerCta * kWarp) {
+          if (lane == 0) my_edges += min(kWarp, e - base);
           const int j = base + lane;
           int u = 0;
           unsigned long long f = 0;
@@ -214,7 +222,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
           }
           acc |= warp_or64(f);
         }
-        if (lane == 0) my_edges += (e - b + kWarpsPerCta - 1) / kWarpsPerCta;
       }
       if (lane == 0) s_or[wib] = acc;
       __syncthreads();
@@ -250,6 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
     const unsigned long long any = s_any;
     __syncthreads();
     if (any == 0) break;
+    active = any;  // the sources whose frontier the next level pulls
     ++l;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) p.st->num_levels = l + 1;
