@@ -46,20 +46,11 @@
 #ifndef S3BFS_CR
 #define S3BFS_CR 2  // candidates per lane per batch of the compaction
 #endif
-#ifndef S3BFS_PREF
-#define S3BFS_PREF 0  // >0: prefetch up to this many 128-byte lines of each lane's row segment into L2
-#endif
-#ifndef S3BFS_PREF_NEXT
-#define S3BFS_PREF_NEXT 0  // >0: same for the row segments of the next window's entries
-#endif
 #ifndef S3BFS_WPC
-#define S3BFS_WPC 32  // warps per CTA (one CTA per SM: one copy of the visited bits)
+#define S3BFS_WPC 32  // warps per CTA of the auxiliary kernels (init, finalize, bitmask batches)
 #endif
 #ifndef S3BFS_HUB_LOG2
 #define S3BFS_HUB_LOG2 18  // visited bits in shared memory for up to 2^this vertices
-#endif
-#ifndef S3BFS_MIN_CTAS
-#define S3BFS_MIN_CTAS 1  // __launch_bounds__ minimum CTAs per SM of the level loop (64 registers)
 #endif
 
 namespace s3bfs {
@@ -252,9 +243,6 @@ __device__ __forceinline__ int4 ld_col4(const int4* p, unsigned long long pol) {
   (void)pol;
   return ld_nc4(p);
 #endif
-}
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 __device__ __forceinline__ long long global_ns() {
   long long t;
@@ -464,29 +452,6 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
       q0 = p0 >> 2;
       nq = ((p1 - 1) >> 2) - q0 + 1;
     }
-#if S3BFS_PREF_NEXT
-    {
-      const int nidx = idx + kWarp;
-      if (nidx < n_l) {
-        const int nex = ld_cg(EX + nidx);
-        const int nex1 = ld_cg(EX + nidx + 1);
-        const int nrs = ld_cg(RS + nidx);
-        const int len = min(nex1, e_end) - nex;
-        if (len > 0) {
-          const int l0 = nrs >> 5, l1 = min((nrs + len - 1) >> 5, l0 + S3BFS_PREF_NEXT - 1);
-          for (int ln = l0; ln <= l1; ++ln) prefetch_l2(p.col_idx + ((long long)ln << 5));
-        }
-      }
-    }
-#endif
-#if S3BFS_PREF
-    // warm L2 with this lane's row segment: the later rounds of the window
-    // then find their quads there
-    if (nq > 0) {
-      const int l0 = p0 >> 5, l1 = min((p1 - 1) >> 5, l0 + S3BFS_PREF - 1);
-      for (int ln = l0; ln <= l1; ++ln) prefetch_l2(p.col_idx + ((long long)ln << 5));
-    }
-#endif
     const int qend = warp_incl_scan(nq, lane);
     const int Q = __shfl_sync(kFull, qend, kWarp - 1);
     const int qoff = qend - nq;
@@ -836,16 +801,7 @@ __device__ __forceinline__ void level_bits(const Params& p, int l, int words, ui
 // Visited bits of vertices [0, hub_n), from the level array after a level's
 // explore (all its level stores are visible).
 __device__ __forceinline__ void build_hub_bits(const Params& p, int gw, int P) {
-#if S3BFS_HUB_BITS_WORDWISE
-  const int lane = threadIdx.x & (kWarp - 1);
-  for (int w = gw; w < (p.hub_n >> 5); w += P) {
-    const int lv = ld_relaxed_nb(p.level + (w << 5) + lane);
-    const unsigned m = __ballot_sync(kFull, lv >= 0);
-    if (lane == 0) p.hub_bits[w] = m;
-  }
-#else
   level_bits(p, -1, p.hub_n >> 5, p.hub_bits, gw, P);
-#endif
 }
 
 // Copies the visited bits into shared memory (whole CTA); returns hub_n.
