@@ -23,6 +23,11 @@ namespace s3bfs {
 constexpr int kMsHeavy = 128;
 constexpr int kMsHuge = 8192;
 constexpr int kMsUnroll = 8;  // neighbour masks in flight per thread (light vertices)
+// dynamic shared memory of k_msbfs when parents are written: per warp, per
+// source bit, per lane, the row offset (< kMsHeavy, one byte) of the first
+// neighbour of the lane's light vertex that carried the bit
+constexpr int kMsParentSmem = kWarpsPerCta * 64 * kWarp;
+static_assert(kMsHeavy <= 256, "light-vertex parent offsets are stored as bytes");
 
 struct MsParams {
   int32_t n, k;
@@ -37,6 +42,7 @@ struct MsParams {
   int32_t* levels_out;           // k x n, source-major, the caller's vertex ids
   int32_t* parents_out;          // k x n or null
   const int32_t* perm;           // internal -> caller id, or null
+  const int32_t* inv;            // caller -> internal id, or null
   unsigned long long* block_or;  // [2][gridDim.x] new bits per CTA, by level parity
   unsigned long long* level_bits;  // [lvl_cap] sources with new vertices at each level
   long long* block_edges;          // [gridDim.x] neighbour entries read, per CTA (whole batch)
@@ -90,12 +96,14 @@ __device__ __forceinline__ void write_bits(const MsParams& p, unsigned long long
 
 // One launch for the whole batch; one grid barrier per level.
 __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
+  extern __shared__ uint8_t ms_dyn[];  // kMsParentSmem bytes when parents_out is set, else none
   __shared__ unsigned long long s_or[kWarpsPerCta];
   __shared__ unsigned long long s_any;
   __shared__ long long s_edges[kWarpsPerCta];
   long long my_edges = 0;
   const int lane = threadIdx.x & (kWarp - 1);
   const int wib = threadIdx.x >> 5;
+  uint8_t* s_off = ms_dyn + wib * 64 * kWarp;  // [source bit][lane]
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;
   const int gw = (int)(tid >> 5);
@@ -113,19 +121,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
     const unsigned long long* cur = par ? p.fr[1] : p.fr[0];
     unsigned long long* nxt = par ? p.fr[0] : p.fr[1];
     unsigned long long my_or = 0;
-    // light vertices: one thread each (the whole warp walks the vertex range
-    // together so that the level stores below coalesce)
+    // light vertices: one thread each.  The whole warp walks the range of
+    // caller ids V0 together, so that the level and parent stores below (rows
+    // of the caller's ids) coalesce; on a renumbered graph the lane pulls for
+    // the internal vertex v = inv[V0].
     const long long n_round = (p.n + nthreads - 1) / nthreads * nthreads;
-    for (long long v = tid; v < n_round; v += nthreads) {
+    for (long long V0 = tid; V0 < n_round; V0 += nthreads) {
+      const long long v = (p.inv && V0 < p.n) ? __ldg(p.inv + V0) : V0;
       unsigned long long nw = 0;
+      int b = 0;
       const bool mine = v < p.n && __ldg(rp + v + 1) - __ldg(rp + v) <= kMsHeavy;
       if (mine) {
-        const int b = __ldg(rp + v), e = __ldg(rp + v + 1);
+        b = __ldg(rp + v);
+        const int e = __ldg(rp + v + 1);
         const unsigned long long s = p.seen[v];
         const unsigned long long need = active & ~s;
         if (need) {
           unsigned long long acc = 0;
-          const int V = out_id(p, (int)v);
           for (int j = b; j < e && (acc & need) != need; j += kMsUnroll) {
             my_edges += min(kMsUnroll, e - j);
             int uu[kMsUnroll];
@@ -137,8 +149,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
 #pragma unroll
             for (int t = 0; t < kMsUnroll; ++t) {
               if (p.parents_out) {
-                const unsigned long long c = ff[t] & ~s & ~acc;
-                if (c) write_bits(p, c, V, out_id(p, uu[t]), p.parents_out);
+                // the first neighbour carrying a new bit is its parent: note
+                // its row offset, the store waits for the warp's bit loop
+                unsigned long long c = ff[t] & ~s & ~acc;
+                while (c) {
+                  const int i = __ffsll((long long)c) - 1;
+                  c &= c - 1;
+                  s_off[i * kWarp + lane] = (uint8_t)(j + t - b);
+                }
               }
               acc |= ff[t];
             }
@@ -149,15 +167,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
         nxt[v] = nw;
         my_or |= nw;
       }
-      // levels of the new (source, vertex) pairs: one store per source bit,
-      // shared by the lanes (consecutive vertices) that found that source
+      // levels and parents of the new (source, vertex) pairs: one store per
+      // source bit, shared by the lanes (consecutive vertices) that found
+      // that source, so the source-major rows are written in runs
       unsigned long long wn = warp_or64(nw);
       if (wn) {
-        const int V = mine ? out_id(p, (int)v) : 0;
+        const int V = (int)V0;
         while (wn) {
           const int i = __ffsll((long long)wn) - 1;
           wn &= wn - 1;
-          if ((nw >> i) & 1ull) p.levels_out[(long long)i * p.n + V] = l + 1;
+          if ((nw >> i) & 1ull) {
+            p.levels_out[(long long)i * p.n + V] = l + 1;
+            if (p.parents_out)
+              p.parents_out[(long long)i * p.n + V] = out_id(p, __ldg(ci + b + s_off[i * kWarp + lane]));
+          }
         }
       }
     }

@@ -880,7 +880,8 @@ static int ms_setup(bfs_graph* g) {
   if (!huge.empty())
     CUDA_TRY(cudaMemcpy(g->d_huge, huge.data(), sizeof(int32_t) * huge.size(), cudaMemcpyHostToDevice));
   int per_sm = 0;
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs, kThreads, 0));
+  CUDA_TRY(cudaFuncSetAttribute(k_msbfs, cudaFuncAttributeMaxDynamicSharedMemorySize, kMsParentSmem));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs, kThreads, kMsParentSmem));
   if (per_sm < 1) return fail(BFS_E_CUDA, "multi-source kernel cannot be resident (occupancy 0)");
   g->ms_ctas = per_sm * g->sms;
   if ((rc = dalloc(g, &g->d_block_or, 2 * (size_t)g->ms_ctas)) != BFS_OK) return rc;
@@ -946,6 +947,7 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
   p.levels_out = L;
   p.parents_out = Pp;
   p.perm = g->relabel ? g->d_perm : nullptr;
+  p.inv = g->relabel ? g->d_inv : nullptr;
   p.block_or = g->d_block_or;
   p.level_bits = g->d_level_bits;
   p.block_edges = g->d_block_edges;
@@ -967,7 +969,8 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
   g->launches = 2;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
   void* args[] = {&p};
-  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_msbfs, dim3(g->ms_ctas), dim3(kThreads), args, 0, g->stream));
+  CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_msbfs, dim3(g->ms_ctas), dim3(kThreads), args,
+                                       Pp ? kMsParentSmem : 0, g->stream));
   ++g->launches;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
   if (stats) {
