@@ -198,7 +198,11 @@ int bfs_run(bfs_graph *g, int32_t src, int32_t *level_out, int32_t *parent_out, 
  * 2 x 64 x n int32 for host output buffers) is allocated at the first such
  * call.  In each stats record of such a group, ms_level_step and ms_total are
  * those of the whole group and candidates = reached - 1.  Otherwise the
- * sources run one after another.
+ * sources run one after another; with host outputs (persistent loop, no
+ * per-level records requested) traversal i's outputs go to the host on a
+ * second stream while traversal i + 1 runs (two device staging slots of
+ * 2 x n int32, allocated at the first such call), so pinned host buffers
+ * cost little beyond the traversals themselves.
  *
  * Errors as for bfs_run; on error the index of the failing source (or group)
  * is in bfs_last_error().

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libs3bfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = [os.path.join(CSRC, f) for f in ("s3bfs.cu", "s3bfs_device.cuh", "msbfs.cuh", "host_internal.h", "serve.cu", "serve_device.cuh", "csr_host.cpp")] + \
+SOURCES = [os.path.join(CSRC, f) for f in ("s3bfs.cu", "level_loop.cuh", "s3bfs_device.cuh", "msbfs.cuh", "host_internal.h", "serve.cu", "serve_device.cuh", "csr_host.cpp")] + \
     [os.path.join(INCLUDE, "s3bfs.h")]
 _lock = threading.Lock()
 

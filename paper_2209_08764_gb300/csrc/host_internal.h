@@ -72,6 +72,14 @@ struct bfs_graph {
   int32_t* d_groups = nullptr;  // vs[64], src_int[64], src_out[64]
   unsigned long long* d_masks = nullptr;
   int32_t *d_stage_level = nullptr, *d_stage_parent = nullptr;  // 64 x n, for host outputs
+  // batches of single-source traversals with host outputs: two staging slots
+  // (level, parent) whose copies to the host overlap the next traversal
+  bool pipe_ready = false;
+  cudaStream_t copy_stream = nullptr;
+  int32_t *d_slot_level[2] = {nullptr, nullptr}, *d_slot_parent[2] = {nullptr, nullptr};
+  cudaEvent_t slot_ev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  cudaEvent_t slot_ready[2] = {nullptr, nullptr}, slot_copied[2] = {nullptr, nullptr};
+  DevState* h_slot_st = nullptr;  // pinned [2]
 };
 
 // last error text of this host thread (bfs_last_error) and its setter

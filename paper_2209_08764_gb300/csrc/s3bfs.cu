@@ -1,6 +1,7 @@
 // S3BFS level-step library for GB300 (sm_103a): kernels and the C ABI.
 //
-// Public interface: include/s3bfs.h.  Device code of the level step:
+// Public interface: include/s3bfs.h.  Kernels: level_loop.cuh (level loop),
+// msbfs.cuh (bitmask batches); their device building blocks:
 // s3bfs_device.cuh.  Host-side CSR checks: csr_host.cpp.
 #include <cuda_runtime.h>
 
@@ -14,6 +15,7 @@
 
 #include "host_internal.h"
 #include "msbfs.cuh"
+#include "level_loop.cuh"
 #include "s3bfs.h"
 #include "s3bfs_device.cuh"
 
@@ -31,8 +33,6 @@ int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, bool sor
 // dynamic shared memory of the level loop: the visited bits
 static size_t loop_smem(int hub_n) { return (size_t)hub_n / 8; }
 
-template <int W, bool DO>
-__global__ void k_level_loop(Params p);
 // the level loop for a CTA shape; DO: with bottom-up levels (a separate
 // kernel, so that the top-down loop carries no trace of them)
 static const void* level_loop_fn(int wpc, bool DO) {
@@ -42,288 +42,6 @@ static const void* level_loop_fn(int wpc, bool DO) {
     case 16: return DO ? (const void*)k_level_loop<16, true> : (const void*)k_level_loop<16, false>;
     default: return DO ? (const void*)k_level_loop<8, true> : (const void*)k_level_loop<8, false>;
   }
-}
-
-// ---------------------------------------------------------------------------
-// kernels
-// ---------------------------------------------------------------------------
-
-// a0 (Fig. 1, initialisation): level = parent = -1 except level[s] = 0, parent[s] =
-// s; F_0 = [s] with its row start and degree; clear the scan and barrier state.
-__global__ void __launch_bounds__(kThreads) k_init(Params p, int ctas) { init_traversal(p, ctas); }
-
-// The whole level loop runs in one cooperative launch (k_level_loop).  A
-// level with at most p.small_edges edges starts a streak that CTA 0 runs
-// alone while the levels stay that small (the others wait at one grid
-// barrier); every other level runs on the whole grid.  Warps beyond P_l skip
-// the level's work and wait at the barrier, so a small level occupies few SMs.
-//
-// One level of the loop (explore, barrier, compact, barrier).  GRID: all
-// CTAs with grid barriers.  Otherwise CTA 0 alone, its warps taking the
-// chunks, with CTA barriers (small levels).  Returns false if the traversal
-// must stop (an error, including a wait that ran out).
-//
-// s_ctrl (shared memory) holds the control block of level l for CTA 0 while
-// it runs small levels alone: it reads the level's sizes from there and the
-// compaction leaves the next level's there, so a small level makes no round
-// trip to global memory for them; the global error word is then read every
-// 32 levels (an error this CTA raises itself shows in s_ctrl).
-template <int W>
-__device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e_l, int* bar, uint32_t* s_hub,
-                                       long long* acc, bool GRID, LevelCtrl* s_ctrl) {
-  __shared__ int s_err;
-  const int lane = threadIdx.x & (kWarp - 1);
-  const int gw = GRID ? blockIdx.x * W + (threadIdx.x >> 5) : (threadIdx.x >> 5);
-  const int P = GRID ? gridDim.x * W : W;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-  const int par = l & 1;
-  int P_l, C_l;
-  level_sizing(e_l, P, p.grain, p.work_insensitive, &P_l, &C_l);
-  long long t_level = 0;
-  if (leader) {
-    t_level = global_ns();
-    acc[0] += n_l;
-    acc[1] += e_l;
-    record_level(p, l, n_l, e_l, P_l);
-  }
-  // big level: take the visited-bits snapshot into shared memory
-  const int hub_lim = (GRID && p.hub_n > 0 && e_l >= p.hub_n) ? load_hub_bits(p, s_hub) : 0;
-  int cnt = 0, e_begin = 0, work = 0;
-  if (gw < P_l) {
-    const long long eb = (long long)gw * C_l;
-    e_begin = (int)min(eb, (long long)e_l);
-    const int e_end = (int)min(eb + C_l, (long long)e_l);
-    work = e_end - e_begin;
-    if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
-  }
-  if (GRID) {
-    if (!grid_sync(p, ++*bar)) return false;
-  } else {
-    __syncthreads();
-  }
-  if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
-  if (GRID && p.hub_n > 0) build_hub_bits(p, gw, P);
-  if (P_l == 0) {
-    if (gw == 0 && lane == 0) {
-      publish_empty_next(p, par);
-      if (!GRID) *s_ctrl = LevelCtrl{0, 0, 0, s_ctrl->cum, 0, 0, 0, s_ctrl->vcum};
-    }
-  } else if (!GRID || (int)blockIdx.x * W < P_l) {
-    compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, GRID ? (int)blockIdx.x : 0, work,
-                   GRID ? nullptr : s_ctrl);
-  }
-  if (GRID) {
-    if (!grid_sync(p, ++*bar)) return false;
-  } else {
-    __syncthreads();
-    if ((l & 31) == 31) {
-      if (threadIdx.x == 0) s_err = ld_relaxed(&p.st->err);
-      __syncthreads();
-      if (s_err != 0) return false;
-    }
-    if (s_ctrl->n < 0) return false;
-  }
-  if (leader) {
-    acc[2] += GRID ? ld_relaxed(&p.st->ctrl[par ^ 1].c) : s_ctrl->c;
-    acc[3] += GRID ? ld_relaxed(&p.st->ctrl[par ^ 1].w) : s_ctrl->w;
-    if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
-  }
-  return true;
-}
-
-// One bottom-up level on the whole grid (direction-optimising traversal of a
-// symmetric graph).  After a top-down level the frontier bitmap is first
-// built from the level array (grid barrier) and every vertex word is
-// scanned; after a bottom-up level only the warps' unvisited lists are.
-// Then (grid barrier) the next level's frontier bitmap is built from the
-// level array while the standard compaction turns the new vertices into the
-// next frontier record and publishes its sizes (grid barrier).  Warp gw's
-// candidates and unvisited list use its own region: room for the 128
-// vertices of every group of four bitmap words it owns.
-template <int W>
-__device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, int* bar, long long* acc) {
-  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
-  const int P = gridDim.x * W;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-  const int par = l & 1;
-  uint32_t* fb_cur = par ? p.fb[1] : p.fb[0];
-  uint32_t* fb_next = par ? p.fb[0] : p.fb[1];
-  long long t_level = 0;
-  if (leader) {
-    t_level = global_ns();
-    acc[0] += n_l;
-    acc[1] += e_l;
-    record_level(p, l, n_l, e_l, P, 1);
-  }
-  const bool after_bu = ld_relaxed(&p.st->ctrl[par].fb) != 0;
-#if S3BFS_BU_BITMAP
-  if (!after_bu) {
-    build_frontier_bits(p, l, fb_cur, gw, P);
-    if (!grid_sync(p, ++*bar)) return false;
-  }
-#endif
-  // warp gw's region: 128 entries per 128-vertex group it owns
-  const int gpw = ((p.nwords >> 2) + P - 1) / P;
-  const long long base = (long long)gw * gpw * 128;
-  int work = 0, first = 0, work0 = 0;
-  const int total = after_bu ? ld_relaxed(p.ulist_cnt + gw)
-                             : bu_unvisited(p, l, fb_cur, gw, P, p.ulist + base, p.cand + base, &first, &work0);
-  const int cnt = first + bu_scan(p, l, fb_cur, gw, total, p.ulist + base, p.cand + base + first, &work,
-                                  after_bu ? 0 : 1);
-  work += __reduce_add_sync(0xffffffffu, work0);
-  if (!grid_sync(p, ++*bar)) return false;
-  if (leader && l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 6] = (int)min(global_ns() - t_level, 2147483647ll);
-#if S3BFS_BU_BITMAP
-  build_frontier_bits(p, l + 1, fb_next, gw, P);
-#else
-  (void)fb_next;
-#endif
-  if (p.hub_n > 0) build_hub_bits(p, gw, P);
-  compact_cta<W>(p, l, par, P, p.cand + base, p.cand_aux + base, cnt, (int)blockIdx.x, work);
-  if (!grid_sync(p, ++*bar)) return false;
-  if (leader) {
-    acc[2] += ld_relaxed(&p.st->ctrl[par ^ 1].c);
-    acc[3] += ld_relaxed(&p.st->ctrl[par ^ 1].w);
-    if (l < p.lvl_cap) p.lvl[(long long)l * kLevelFields + 5] = (int)min(global_ns() - t_level, 2147483647ll);
-  }
-  return true;
-}
-
-// 8-warp CTAs: four per SM (64 registers a thread); wider CTAs: one per SM
-// (64, 80 or 128 registers a thread with 32, 24 or 16 warps)
-template <int W, bool DO>
-__global__ void __launch_bounds__(W * kWarp, W == 8 ? 4 : 1) k_level_loop(Params p) {
-  extern __shared__ __align__(16) uint32_t s_hub[];  // visited bits, p.hub_n / 8 bytes
-  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
-  const int P = gridDim.x * W;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-  if (threadIdx.x == 0) p.cta_smid[blockIdx.x] = sm_id();
-  __shared__ LevelCtrl s_ctrl;  // CTA 0 during a streak: the current level's control block
-  int bar = 0, l = 0;
-  long long acc[4] = {0, 0, 0, 0};  // reached, edges, candidates, work (leader)
-  bool streak = false;           // CTA 0 is running small levels alone
-  while (true) {
-    int n_l, e_l;
-    bool bottom_up;
-    if (streak) {
-      n_l = s_ctrl.n;
-      e_l = s_ctrl.e;
-      bottom_up = s_ctrl.dir != 0;
-    } else {
-      n_l = ld_relaxed(&p.st->ctrl[l & 1].n);
-      e_l = ld_relaxed(&p.st->ctrl[l & 1].e);
-      bottom_up = ld_relaxed(&p.st->ctrl[l & 1].dir) != 0;
-    }
-    const bool small = n_l > 0 && p.small_edges > 0 && e_l <= p.small_edges && !bottom_up;
-    if (streak && !small) {
-      // CTA 0 ends its streak: the whole grid resumes at level l (or stops)
-      streak = false;
-      if (threadIdx.x == 0) st_relaxed(&p.st->resume_level, l);
-      if (!grid_sync(p, ++bar)) break;
-      if (p.hub_n > 0) {
-        // the visited bits were not kept up to date by the streak
-        build_hub_bits(p, gw, P);
-        if (!grid_sync(p, ++bar)) break;
-      }
-      continue;
-    }
-    if (n_l <= 0) break;
-    if (l + 2 >= (int)kEpochMask) {
-      if (leader) set_err(p, BFS_E_INVAL, 5);
-      break;
-    }
-    if (small && blockIdx.x != 0) {
-      // parked at one grid barrier while CTA 0 runs the small levels
-      if (!grid_sync(p, ++bar)) break;
-      l = ld_relaxed(&p.st->resume_level);
-      if (p.hub_n > 0) {
-        build_hub_bits(p, gw, P);
-        if (!grid_sync(p, ++bar)) break;
-      }
-      continue;
-    }
-    if (DO && bottom_up) {
-      if (!bu_level<W>(p, l, n_l, e_l, &bar, acc)) break;
-      ++l;
-      continue;
-    }
-    if (small && !streak) {
-      // a streak starts: its control blocks live in shared memory
-      if (threadIdx.x == 0) {
-        const LevelCtrl* c = &p.st->ctrl[l & 1];
-        s_ctrl = LevelCtrl{n_l, e_l, 0, ld_relaxed(&c->cum), 0, 0, 0, ld_relaxed(&c->vcum)};
-      }
-      __syncthreads();
-    }
-    streak = small;
-    if (!one_level<W>(p, l, n_l, e_l, &bar, s_hub, acc, !small, &s_ctrl)) {
-      if (streak) {
-        // release the parked CTAs; the error word makes everybody stop
-        if (threadIdx.x == 0) st_relaxed(&p.st->resume_level, l);
-        grid_sync(p, ++bar);
-      }
-      break;
-    }
-    ++l;
-    if (small && threadIdx.x == 0) st_relaxed(&p.st->progress, l);
-  }
-  if (leader) {
-    p.st->num_levels = l;
-    p.st->reached = acc[0];
-    p.st->edges = acc[1];
-    p.st->cands = acc[2];
-    p.st->work = acc[3];
-  }
-}
-
-// Launch-per-phase mode: the same two phases as separate launches; the host
-// reads n and e of the next level in between.
-template <int W>
-__global__ void __launch_bounds__(W * kWarp) k_explore(Params p, int l, int n_l, int e_l, int P_l, int C_l) {
-  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
-  if (blockIdx.x == 0 && threadIdx.x == 0) record_level(p, l, n_l, e_l, P_l);
-  if (gw >= P_l) return;
-  const long long eb = (long long)gw * C_l;
-  const int e_begin = (int)min(eb, (long long)e_l);
-  const int e_end = (int)min(eb + C_l, (long long)e_l);
-  int cnt = 0;
-  if (e_begin < e_end) cnt = explore_chunk(p, l, l & 1, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
-  if ((threadIdx.x & (kWarp - 1)) == 0) p.cand_cnt[gw] = cnt;
-}
-
-template <int W>
-__global__ void __launch_bounds__(W * kWarp) k_compact(Params p, int l, int e_l, int P_l, int C_l) {
-  const int gw = blockIdx.x * W + (threadIdx.x >> 5);
-  const int par = l & 1;
-  if (P_l == 0) {
-    if (gw == 0 && (threadIdx.x & (kWarp - 1)) == 0) publish_empty_next(p, par);
-    return;
-  }
-  // every thread of the CTA takes part; warps without a chunk bring 0
-  const int e_begin = gw < P_l ? (int)min((long long)gw * C_l, (long long)e_l) : 0;
-  const int e_end = gw < P_l ? (int)min((long long)gw * C_l + C_l, (long long)e_l) : 0;
-  const int cnt = gw < P_l ? ld_relaxed(&p.cand_cnt[gw]) : 0;
-  compact_cta<W>(p, l, par, P_l, p.cand + e_begin, p.cand_aux + e_begin, cnt, (int)blockIdx.x, e_end - e_begin);
-}
-
-// CSR sanity checks that every traversal relies on (no out-of-range access):
-// row_ptr starts at 0, never decreases, ends at nnz; 0 <= col_idx < n.
-__global__ void k_check_csr(int32_t n, int32_t nnz, const int32_t* rp, const int32_t* ci, int* bad) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  if (tid == 0 && (rp[0] != 0 || rp[n] != nnz)) *bad = 1;
-  for (long long i = tid; i < n; i += stride)
-    if (rp[i] > rp[i + 1]) *bad = 1;
-  for (long long e = tid; e < nnz; e += stride)
-    if ((unsigned)ci[e] >= (unsigned)n) *bad = 2;
-}
-
-// Outputs of a renumbered graph back in the caller's vertex ids: v is the
-// caller's id, inv[v] the internal one, perm[i] the caller's id of internal i.
-__global__ void __launch_bounds__(kThreads) k_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
-                                                       const int32_t* level, const int32_t* parent,
-                                                       int32_t* level_out, int32_t* parent_out) {
-  finalize_outputs(n, inv, perm, level, parent, level_out, parent_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -375,6 +93,17 @@ extern "C" void bfs_destroy(bfs_graph* g) {
   if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
+  if (g->copy_stream) {
+    cudaStreamSynchronize(g->copy_stream);
+    cudaStreamDestroy(g->copy_stream);
+  }
+  for (int s = 0; s < 2; ++s) {
+    for (auto& e : g->slot_ev[s])
+      if (e) cudaEventDestroy(e);
+    if (g->slot_ready[s]) cudaEventDestroy(g->slot_ready[s]);
+    if (g->slot_copied[s]) cudaEventDestroy(g->slot_copied[s]);
+  }
+  if (g->h_slot_st) cudaFreeHost(g->h_slot_st);
   cudaSetDevice(cur);
   delete g;
 }
@@ -678,13 +407,16 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
 }
 
 // Enqueue one traversal (init + level loop) on the graph's stream.
-static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
+// ev: three events recorded before init, before the level loop and after it
+// (null: untimed)
+static int enqueue_traversal(bfs_graph* g, const Params& p, cudaEvent_t* ev) {
+  const bool timed = ev != nullptr;
+  if (timed) CUDA_TRY(cudaEventRecord(ev[0], g->stream));
   const int igrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n / 4 + 255) / 256)));
   k_init<<<igrid, kThreads, 0, g->stream>>>(p, g->ctas);
   CUDA_TRY(cudaGetLastError());
   ++g->launches;
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[1], g->stream));
+  if (timed) CUDA_TRY(cudaEventRecord(ev[1], g->stream));
   if (g->persistent) {
     Params pc = p;
     void* args[] = {&pc};
@@ -749,7 +481,34 @@ static int enqueue_traversal(bfs_graph* g, const Params& p, bool timed) {
     CUDA_TRY(cudaStreamSynchronize(g->stream));
   }
   CUDA_TRY(cudaGetLastError());
-  if (timed) CUDA_TRY(cudaEventRecord(g->ev[2], g->stream));
+  if (timed) CUDA_TRY(cudaEventRecord(ev[2], g->stream));
+  return BFS_OK;
+}
+
+// The traversal's outcome from its device state block (copied to the host).
+static int traversal_error(const DevState& st, int32_t src) {
+  if (st.err == 0) return BFS_OK;
+  if (st.err == BFS_E_TIMEOUT) return fail(BFS_E_TIMEOUT, "device wait %d ran out (src %d)", st.err_where, src);
+  if (st.err == BFS_E_MULTIGRAPH)
+    return fail(BFS_E_MULTIGRAPH, "next frontier larger than n: the graph repeats a neighbour (src %d)", src);
+  return fail(st.err, "device error %d at %d (src %d)", st.err, st.err_where, src);
+}
+
+// Totals and times of a finished traversal (ev: its three events, or null).
+static int traversal_stats(const bfs_graph* g, const DevState& st, int launches, cudaEvent_t* ev, bfs_stats* stats) {
+  stats->num_levels = st.num_levels;
+  stats->active_ctas = g->persistent ? g->ctas : 0;
+  stats->reached = st.reached;
+  stats->edges_scanned = st.edges;
+  stats->candidates = st.cands;
+  stats->ms_level_step = 0.f;
+  stats->ms_total = 0.f;
+  stats->work_edges = st.work;
+  stats->launches = launches;
+  if (ev) {
+    CUDA_TRY(cudaEventElapsedTime(&stats->ms_level_step, ev[1], ev[2]));
+    CUDA_TRY(cudaEventElapsedTime(&stats->ms_total, ev[0], ev[2]));
+  }
   return BFS_OK;
 }
 
@@ -760,26 +519,9 @@ static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t 
                              g->stream));
   CUDA_TRY(cudaStreamSynchronize(g->stream));
   const DevState& st = *g->h_st;
-  if (st.err != 0) {
-    if (st.err == BFS_E_TIMEOUT) return fail(BFS_E_TIMEOUT, "device wait %d ran out (src %d)", st.err_where, src);
-    if (st.err == BFS_E_MULTIGRAPH)
-      return fail(BFS_E_MULTIGRAPH, "next frontier larger than n: the graph repeats a neighbour (src %d)", src);
-    return fail(st.err, "device error %d at %d (src %d)", st.err, st.err_where, src);
-  }
-  if (!stats) return BFS_OK;
-  stats->num_levels = st.num_levels;
-  stats->active_ctas = g->persistent ? g->ctas : 0;
-  stats->reached = st.reached;
-  stats->edges_scanned = st.edges;
-  stats->candidates = st.cands;
-  stats->ms_level_step = 0.f;
-  stats->ms_total = 0.f;
-  stats->work_edges = st.work;
-  stats->launches = g->launches;
-  if (timed) {
-    CUDA_TRY(cudaEventElapsedTime(&stats->ms_level_step, g->ev[1], g->ev[2]));
-    CUDA_TRY(cudaEventElapsedTime(&stats->ms_total, g->ev[0], g->ev[2]));
-  }
+  int rc = traversal_error(st, src);
+  if (rc != BFS_OK || !stats) return rc;
+  if ((rc = traversal_stats(g, st, g->launches, timed ? g->ev : nullptr, stats)) != BFS_OK) return rc;
   if (stats->per_level && stats->per_level_cap > 0) {
     const int L = std::min(std::min(st.num_levels, stats->per_level_cap), g->lvl_cap);
     if (L > 0)
@@ -818,7 +560,7 @@ static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* paren
   const Params p = make_params(g, g->relabel ? g->h_inv[src] : src, level, parent);
   const bool timed = stats != nullptr;
   g->launches = 0;
-  int rc = enqueue_traversal(g, p, timed);
+  int rc = enqueue_traversal(g, p, timed ? g->ev : nullptr);
   if (rc != BFS_OK) return rc;
   const int32_t* lvl_src = level;
   const int32_t* par_src = parent;
@@ -1023,6 +765,98 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
   return BFS_OK;
 }
 
+// ---- batches of single-source traversals with host outputs ---------------
+//
+// Traversal i runs on the graph's stream into staging slot i & 1 (directly,
+// or through k_finalize on a renumbered graph); its device state block is
+// copied to a pinned slot and an event marks it done.  A second stream
+// waits for that event and copies the slot to the caller's buffers while
+// traversal i + 1 runs; traversal i + 2 waits for that copy before it
+// reuses the slot.  The host checks traversal i - 1 (error, stats) after
+// it has queued traversal i, so the GPU is never idle on the host.
+// Copies into pageable host memory are correct but do not overlap.
+
+static int pipe_setup(bfs_graph* g) {
+  if (g->pipe_ready) return BFS_OK;
+  int rc;
+  for (int s = 0; s < 2; ++s) {
+    if ((rc = dalloc(g, &g->d_slot_level[s], (size_t)g->n + 4)) != BFS_OK) return rc;
+    if ((rc = dalloc(g, &g->d_slot_parent[s], (size_t)g->n + 4)) != BFS_OK) return rc;
+    for (auto& e : g->slot_ev[s]) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventCreateWithFlags(&g->slot_ready[s], cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&g->slot_copied[s], cudaEventDisableTiming));
+  }
+  CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  if (cudaHostAlloc((void**)&g->h_slot_st, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    g->h_slot_st = nullptr;
+    return fail(BFS_E_NOMEM, "pinned host allocation failed");
+  }
+  g->pipe_ready = true;
+  return BFS_OK;
+}
+
+static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int32_t* levels_out,
+                               int32_t* parents_out, bfs_stats* stats) {
+  int rc = pipe_setup(g);
+  if (rc != BFS_OK) return rc;
+  const size_t n = (size_t)g->n;
+  int launches[2] = {0, 0};
+  // wait for traversal i and its copy, then check it
+  auto finish = [&](int32_t i) -> int {
+    const int s = i & 1;
+    CUDA_TRY(cudaEventSynchronize(g->slot_copied[s]));
+    const DevState& st = g->h_slot_st[s];
+    int r = traversal_error(st, srcs[i]);
+    if (r == BFS_OK && stats) r = traversal_stats(g, st, launches[s], g->slot_ev[s], stats + i);
+    return r;
+  };
+  int32_t failed = -1;
+  for (int32_t i = 0; i < k && rc == BFS_OK; ++i) {
+    const int s = i & 1;
+    if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[s], 0));
+    int32_t* lw = g->relabel ? g->d_level : g->d_slot_level[s];
+    int32_t* pw = (g->relabel || !parents_out) ? g->d_parent : g->d_slot_parent[s];
+    const Params p = make_params(g, g->relabel ? g->h_inv[srcs[i]] : srcs[i], lw, pw);
+    g->launches = 0;
+    rc = enqueue_traversal(g, p, stats ? g->slot_ev[s] : nullptr);
+    if (rc != BFS_OK) {
+      failed = i;
+      break;
+    }
+    if (g->relabel) {
+      const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
+      k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, lw, pw, g->d_slot_level[s],
+                                                     parents_out ? g->d_slot_parent[s] : nullptr);
+      CUDA_TRY(cudaGetLastError());
+      ++g->launches;
+    }
+    launches[s] = g->launches;
+    CUDA_TRY(cudaMemcpyAsync(&g->h_slot_st[s], g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaEventRecord(g->slot_ready[s], g->stream));
+    CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, g->slot_ready[s], 0));
+    CUDA_TRY(cudaMemcpyAsync(levels_out + (size_t)i * n, g->d_slot_level[s], sizeof(int32_t) * n,
+                             cudaMemcpyDeviceToHost, g->copy_stream));
+    if (parents_out)
+      CUDA_TRY(cudaMemcpyAsync(parents_out + (size_t)i * n, g->d_slot_parent[s], sizeof(int32_t) * n,
+                               cudaMemcpyDeviceToHost, g->copy_stream));
+    CUDA_TRY(cudaEventRecord(g->slot_copied[s], g->copy_stream));
+    if (i >= 1 && (rc = finish(i - 1)) != BFS_OK) failed = i - 1;
+  }
+  if (rc == BFS_OK && k >= 1 && (rc = finish(k - 1)) != BFS_OK) failed = k - 1;
+  if (rc != BFS_OK) {
+    // nothing of this call stays in flight
+    cudaStreamSynchronize(g->stream);
+    cudaStreamSynchronize(g->copy_stream);
+    if (failed >= 0) {
+      char keep[sizeof(g_last_error) - 32];
+      snprintf(keep, sizeof(keep), "%.*s", (int)sizeof(keep) - 1, g_last_error);
+      snprintf(g_last_error, sizeof(g_last_error), "source index %d: %s", failed, keep);
+    }
+  }
+  return rc;
+}
+
 extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32_t* levels_out,
                              int32_t* parents_out, bfs_stats* stats) {
   if (!g) return fail(BFS_E_INVAL, "graph is NULL");
@@ -1041,6 +875,15 @@ extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32
       rc = run_group_bitmask(g, srcs + i, kk, levels_out + (size_t)i * g->n,
                              parents_out ? parents_out + (size_t)i * g->n : nullptr, stats ? stats + i : nullptr);
     }
+    if (cur != g->device) cudaSetDevice(cur);
+    return rc;
+  }
+  // host outputs: overlap each traversal's copy with the next traversal
+  bool per_level = false;
+  for (int32_t i = 0; stats && i < k; ++i) per_level |= stats[i].per_level && stats[i].per_level_cap > 0;
+  if (k >= 2 && g->persistent && !per_level && !is_device_ptr(levels_out) &&
+      (!parents_out || !is_device_ptr(parents_out))) {
+    rc = run_batch_pipelined(g, srcs, k, levels_out, parents_out, stats);
     if (cur != g->device) cudaSetDevice(cur);
     return rc;
   }

@@ -42,3 +42,9 @@ def test_workloads_are_the_documented_configurations():
     assert (w["scale"], w["edgefactor"], w["sources"], w["seed"], w["src_seed"]) == (22, 16, 64, 1, 2)
     assert bench.WORKLOADS["grid4096"]["rows"] == bench.WORKLOADS["grid4096"]["cols"] == 4096
     assert bench.WORKLOADS["er20"]["m"] == 8 << 20
+
+
+def test_cpulist_parsing():
+    assert bench.parse_cpulist("0-3,8,10-11") == [0, 1, 2, 3, 8, 10, 11]
+    assert bench.parse_cpulist("72-143\n") == list(range(72, 144))
+    assert bench.parse_cpulist("") == []

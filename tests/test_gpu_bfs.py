@@ -224,6 +224,74 @@ def test_run_batch_matches_single_runs(rmat16, relabel):
         d.close()
 
 
+@pytest.mark.parametrize("relabel", [-1, 1])
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("parents", [True, False])
+def test_run_batch_host_outputs_overlapped(rmat16, relabel, pinned, parents):
+    """Host outputs of a batch of single-source traversals: each traversal's
+    copy to the host runs while the next traversal runs (two staging slots,
+    a copy stream).  Every source's levels equal the oracle's, its parents
+    form a BFS tree, and its stats are its own."""
+    import torch
+    rp, ci, srcs, keys = rmat16
+    d = Dev(rp, ci, relabel=relabel)
+    try:
+        k = 7  # odd: both slots, the last one used once more
+        S = np.ascontiguousarray(srcs[:k])
+        if pinned:
+            L = torch.full((k * d.n,), -7, dtype=torch.int32, pin_memory=True)
+            P = torch.full((k * d.n,), -7, dtype=torch.int32, pin_memory=True) if parents else None
+        else:
+            L = np.full(k * d.n, -7, np.int32)
+            P = np.full(k * d.n, -7, np.int32) if parents else None
+        st = (B.bfs_stats * k)()
+        B.bfs_run_batch(d.g, S, k, L, P, st)
+        L = np.asarray(L).reshape(k, d.n)
+        orc = oracle.Oracle(rp, ci)
+        for i, s in enumerate(S):
+            want, _ = orc.bfs(int(s))
+            assert np.array_equal(L[i], want), f"source {i}"
+            if parents:
+                oracle.check_bfs_tree(rp, ci, int(s), L[i], np.asarray(P).reshape(k, d.n)[i], keys=keys)
+            n_l, e_l = oracle.level_profile(rp, want)
+            assert st[i].reached == int(n_l.sum()) and st[i].num_levels == len(n_l)
+            assert st[i].edges_scanned == int(e_l.sum())
+            assert 0 < st[i].ms_level_step <= st[i].ms_total
+            assert st[i].launches >= 2
+        # the same handle then serves single runs and a batch without stats
+        check_against_oracle(d, int(S[0]))
+        Lh = np.empty((2, d.n), np.int32)
+        B.bfs_run_batch(d.g, S[:2], 2, Lh, None, None)
+        assert np.array_equal(Lh[1], orc.bfs(int(S[1]))[0])
+    finally:
+        d.close()
+
+
+def test_run_batch_host_outputs_timeout_names_the_source():
+    """An overlapped batch whose traversals time out (test hook: a CTA never
+    arrives at the first barrier): the error and the failing source index
+    come back, nothing stays in flight, and a new handle works."""
+    rp, ci = graphgen.rmat(10, 16, seed=1)
+    S = np.ascontiguousarray(graphgen.sample_sources(rp, 3), np.int32)
+    d = Dev(rp, ci, debug_flags=B.BFS_DEBUG_STALL_BARRIER, spin_limit_ms=200, ctas=4)
+    try:
+        L = np.empty(3 * d.n, np.int32)
+        with pytest.raises(B.BFSError) as e:
+            B.bfs_run_batch(d.g, S, 3, L, None, None)
+        assert e.value.code == B.BFS_E_TIMEOUT
+        assert "source index 0" in B.bfs_last_error()
+    finally:
+        d.close()
+    d = Dev(rp, ci)
+    try:
+        L = np.empty(3 * d.n, np.int32)
+        B.bfs_run_batch(d.g, S, 3, L, None, None)
+        for i, s in enumerate(S):
+            assert np.array_equal(L[i * d.n:(i + 1) * d.n], oracle.bfs(rp, ci, int(s))[0])
+    finally:
+        d.close()
+
+
 @pytest.mark.parametrize("small", [-1, 0, 1 << 20])
 @pytest.mark.parametrize("cw", [8, 16, 32])
 def test_long_path_and_grid_small_level_mode(small, cw):
