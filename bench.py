@@ -727,22 +727,26 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     # host check: the generators' output is symmetric and simple, which the
     # CPU tests of graphgen pin.
     flags = B.BFS_SYMMETRIC if direction else B.BFS_VALIDATE
+    opts.batch_bitmask = -1  # a batch here is single-source traversals, never one bitmask traversal
     t_create = time.perf_counter()
     g = B.bfs_create_csr(n, nnz, rp, ci, flags, opts, stream.cuda_stream)
     t_create = time.perf_counter() - t_create
     info = B.bfs_graph_info(g)
     level = torch.empty(n, dtype=torch.int32, device=dev)
     parent = torch.empty(n, dtype=torch.int32, device=dev)
-    st = B.bfs_stats()
+    # one step = one bfs_run_batch over the sources: single-source traversals
+    # queued back to back, every one writing its own level and parent arrays
+    S = np.ascontiguousarray(srcs, np.int32)
+    L_all = torch.empty(len(S) * n, dtype=torch.int32, device=dev)
+    P_all = torch.empty(len(S) * n, dtype=torch.int32, device=dev)
+    st_all = (B.bfs_stats * len(S))()
 
     def step(record):
-        out = []
-        for s in srcs:
-            B.bfs_run(g, int(s), level, parent, st)
-            if record is not None:
-                out.append((st.ms_level_step, st.ms_total, st.reached, st.edges_scanned, st.candidates,
-                            st.num_levels, int(s), st.launches, st.work_edges))
-        return out
+        B.bfs_run_batch(g, S, len(S), L_all, P_all, st_all if record is not None else None)
+        if record is None:
+            return []
+        return [(st.ms_level_step, st.ms_total, st.reached, st.edges_scanned, st.candidates, st.num_levels,
+                 int(S[i]), st.launches, st.work_edges) for i, st in enumerate(st_all)]
 
     for _ in range(args.warmup):
         step(None)
@@ -837,8 +841,17 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
         for _ in range(args.steps):
             B.bfs_run_batch(g, S, len(S), hl, hp, None)
         te = time.perf_counter() - t0
+        # this box's plain device -> pinned host copy rate (one traversal's
+        # level array, 8 times), beside which the end-to-end number is read
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(8):
+            hl[:n].copy_(L_all[:n], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        d2h_gbs = 8 * 4 * n / (e0.elapsed_time(e1) / 1e3) / 1e9
         e2e = {"value": edges_per_step * args.steps / te / 1e9, "unit": "GTEPS",
-               "cpu_affinity": getattr(args, "cpu_affinity", None),
+               "d2h_copy_gbs": round(d2h_gbs, 1), "cpu_affinity": getattr(args, "cpu_affinity", None),
                "h2d_bytes_per_step": 4 * len(srcs),
                "d2h_bytes_per_step": int(len(srcs) * (8 * n + ctypes.sizeof(ctypes.c_int64) * 8))}
 

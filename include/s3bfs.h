@@ -198,11 +198,13 @@ int bfs_run(bfs_graph *g, int32_t src, int32_t *level_out, int32_t *parent_out, 
  * 2 x 64 x n int32 for host output buffers) is allocated at the first such
  * call.  In each stats record of such a group, ms_level_step and ms_total are
  * those of the whole group and candidates = reached - 1.  Otherwise the
- * sources run one after another; with host outputs (persistent loop, no
- * per-level records requested) traversal i's outputs go to the host on a
- * second stream while traversal i + 1 runs (two device staging slots of
- * 2 x n int32, allocated at the first such call), so pinned host buffers
- * cost little beyond the traversals themselves.
+ * sources run one after another.  With the persistent loop, no per-level
+ * records requested and both outputs on the same side (device or host), the
+ * traversals are queued back to back: the host checks traversal i - 1 while
+ * traversal i runs.  Host outputs then go through two device staging slots
+ * (2 x n int32 each, allocated at the first such call) and a second stream
+ * copies traversal i's outputs while traversal i + 1 runs, so pinned host
+ * buffers cost little beyond the traversals themselves.
  *
  * Errors as for bfs_run; on error the index of the failing source (or group)
  * is in bfs_last_error().

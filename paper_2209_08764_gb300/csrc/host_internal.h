@@ -72,8 +72,9 @@ struct bfs_graph {
   int32_t* d_groups = nullptr;  // vs[64], src_int[64], src_out[64]
   unsigned long long* d_masks = nullptr;
   int32_t *d_stage_level = nullptr, *d_stage_parent = nullptr;  // 64 x n, for host outputs
-  // batches of single-source traversals with host outputs: two staging slots
-  // (level, parent) whose copies to the host overlap the next traversal
+  // batches of single-source traversals queued back to back: per slot (i & 1)
+  // events and a pinned state block; with host outputs also a device staging
+  // pair (level, parent) whose copy to the host overlaps the next traversal
   bool pipe_ready = false;
   cudaStream_t copy_stream = nullptr;
   int32_t *d_slot_level[2] = {nullptr, nullptr}, *d_slot_parent[2] = {nullptr, nullptr};

@@ -765,23 +765,28 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
   return BFS_OK;
 }
 
-// ---- batches of single-source traversals with host outputs ---------------
+// ---- batches of single-source traversals, queued back to back -----------
 //
-// Traversal i runs on the graph's stream into staging slot i & 1 (directly,
-// or through k_finalize on a renumbered graph); its device state block is
-// copied to a pinned slot and an event marks it done.  A second stream
-// waits for that event and copies the slot to the caller's buffers while
-// traversal i + 1 runs; traversal i + 2 waits for that copy before it
-// reuses the slot.  The host checks traversal i - 1 (error, stats) after
-// it has queued traversal i, so the GPU is never idle on the host.
-// Copies into pageable host memory are correct but do not overlap.
+// Traversal i runs on the graph's stream, its device state block is copied
+// to pinned slot i & 1 and an event marks it done; the host checks traversal
+// i - 1 (error, stats) only after it has queued traversal i, so the GPU does
+// not wait for the host between traversals.  Device outputs are written in
+// place (through k_finalize on a renumbered graph).  Host outputs go through
+// device staging slot i & 1: a second stream copies the slot to the caller's
+// buffers while traversal i + 1 runs, and traversal i + 2 waits for that copy
+// before it reuses the slot.  Copies into pageable host memory are correct
+// but do not overlap.
 
-static int pipe_setup(bfs_graph* g) {
-  if (g->pipe_ready) return BFS_OK;
+static int pipe_setup(bfs_graph* g, bool host) {
   int rc;
+  if (host && !g->d_slot_level[1]) {
+    for (int s = 0; s < 2; ++s) {
+      if ((rc = dalloc(g, &g->d_slot_level[s], (size_t)g->n + 4)) != BFS_OK) return rc;
+      if ((rc = dalloc(g, &g->d_slot_parent[s], (size_t)g->n + 4)) != BFS_OK) return rc;
+    }
+  }
+  if (g->pipe_ready) return BFS_OK;
   for (int s = 0; s < 2; ++s) {
-    if ((rc = dalloc(g, &g->d_slot_level[s], (size_t)g->n + 4)) != BFS_OK) return rc;
-    if ((rc = dalloc(g, &g->d_slot_parent[s], (size_t)g->n + 4)) != BFS_OK) return rc;
     for (auto& e : g->slot_ev[s]) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventCreateWithFlags(&g->slot_ready[s], cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&g->slot_copied[s], cudaEventDisableTiming));
@@ -797,15 +802,15 @@ static int pipe_setup(bfs_graph* g) {
 }
 
 static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int32_t* levels_out,
-                               int32_t* parents_out, bfs_stats* stats) {
-  int rc = pipe_setup(g);
+                               int32_t* parents_out, bfs_stats* stats, bool host) {
+  int rc = pipe_setup(g, host);
   if (rc != BFS_OK) return rc;
   const size_t n = (size_t)g->n;
   int launches[2] = {0, 0};
-  // wait for traversal i and its copy, then check it
+  // wait for traversal i (and its copy), then check it
   auto finish = [&](int32_t i) -> int {
     const int s = i & 1;
-    CUDA_TRY(cudaEventSynchronize(g->slot_copied[s]));
+    CUDA_TRY(cudaEventSynchronize(host ? g->slot_copied[s] : g->slot_ready[s]));
     const DevState& st = g->h_slot_st[s];
     int r = traversal_error(st, srcs[i]);
     if (r == BFS_OK && stats) r = traversal_stats(g, st, launches[s], g->slot_ev[s], stats + i);
@@ -814,9 +819,12 @@ static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int
   int32_t failed = -1;
   for (int32_t i = 0; i < k && rc == BFS_OK; ++i) {
     const int s = i & 1;
-    if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[s], 0));
-    int32_t* lw = g->relabel ? g->d_level : g->d_slot_level[s];
-    int32_t* pw = (g->relabel || !parents_out) ? g->d_parent : g->d_slot_parent[s];
+    if (host && i >= 2) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[s], 0));
+    // this traversal's outputs on the device, and its working arrays
+    int32_t* lo = host ? g->d_slot_level[s] : levels_out + (size_t)i * n;
+    int32_t* po = parents_out ? (host ? g->d_slot_parent[s] : parents_out + (size_t)i * n) : nullptr;
+    int32_t* lw = g->relabel ? g->d_level : lo;
+    int32_t* pw = (g->relabel || !po) ? g->d_parent : po;
     const Params p = make_params(g, g->relabel ? g->h_inv[srcs[i]] : srcs[i], lw, pw);
     g->launches = 0;
     rc = enqueue_traversal(g, p, stats ? g->slot_ev[s] : nullptr);
@@ -826,21 +834,22 @@ static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int
     }
     if (g->relabel) {
       const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
-      k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, lw, pw, g->d_slot_level[s],
-                                                     parents_out ? g->d_slot_parent[s] : nullptr);
+      k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, lw, pw, lo, po);
       CUDA_TRY(cudaGetLastError());
       ++g->launches;
     }
     launches[s] = g->launches;
     CUDA_TRY(cudaMemcpyAsync(&g->h_slot_st[s], g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaEventRecord(g->slot_ready[s], g->stream));
-    CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, g->slot_ready[s], 0));
-    CUDA_TRY(cudaMemcpyAsync(levels_out + (size_t)i * n, g->d_slot_level[s], sizeof(int32_t) * n,
-                             cudaMemcpyDeviceToHost, g->copy_stream));
-    if (parents_out)
-      CUDA_TRY(cudaMemcpyAsync(parents_out + (size_t)i * n, g->d_slot_parent[s], sizeof(int32_t) * n,
-                               cudaMemcpyDeviceToHost, g->copy_stream));
-    CUDA_TRY(cudaEventRecord(g->slot_copied[s], g->copy_stream));
+    if (host) {
+      CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, g->slot_ready[s], 0));
+      CUDA_TRY(cudaMemcpyAsync(levels_out + (size_t)i * n, lo, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                               g->copy_stream));
+      if (po)
+        CUDA_TRY(cudaMemcpyAsync(parents_out + (size_t)i * n, po, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                 g->copy_stream));
+      CUDA_TRY(cudaEventRecord(g->slot_copied[s], g->copy_stream));
+    }
     if (i >= 1 && (rc = finish(i - 1)) != BFS_OK) failed = i - 1;
   }
   if (rc == BFS_OK && k >= 1 && (rc = finish(k - 1)) != BFS_OK) failed = k - 1;
@@ -878,12 +887,13 @@ extern "C" int bfs_run_batch(bfs_graph* g, const int32_t* srcs, int32_t k, int32
     if (cur != g->device) cudaSetDevice(cur);
     return rc;
   }
-  // host outputs: overlap each traversal's copy with the next traversal
+  // traversals queued back to back (host outputs: copies overlapped), unless
+  // per-level records are wanted or the outputs mix device and host memory
   bool per_level = false;
   for (int32_t i = 0; stats && i < k; ++i) per_level |= stats[i].per_level && stats[i].per_level_cap > 0;
-  if (k >= 2 && g->persistent && !per_level && !is_device_ptr(levels_out) &&
-      (!parents_out || !is_device_ptr(parents_out))) {
-    rc = run_batch_pipelined(g, srcs, k, levels_out, parents_out, stats);
+  const bool lvl_dev = is_device_ptr(levels_out);
+  if (k >= 2 && g->persistent && !per_level && (!parents_out || is_device_ptr(parents_out) == lvl_dev)) {
+    rc = run_batch_pipelined(g, srcs, k, levels_out, parents_out, stats, !lvl_dev);
     if (cur != g->device) cudaSetDevice(cur);
     return rc;
   }

@@ -225,27 +225,33 @@ def test_run_batch_matches_single_runs(rmat16, relabel):
 
 
 @pytest.mark.parametrize("relabel", [-1, 1])
-@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("where", ["pinned", "pageable", "device"])
 @pytest.mark.parametrize("parents", [True, False])
-def test_run_batch_host_outputs_overlapped(rmat16, relabel, pinned, parents):
-    """Host outputs of a batch of single-source traversals: each traversal's
-    copy to the host runs while the next traversal runs (two staging slots,
-    a copy stream).  Every source's levels equal the oracle's, its parents
-    form a BFS tree, and its stats are its own."""
+def test_run_batch_queued_back_to_back(rmat16, relabel, where, parents):
+    """A batch of single-source traversals queued back to back (the host
+    checks traversal i - 1 while traversal i runs); host outputs are copied
+    from two staging slots on a second stream while the next traversal runs.
+    Every source's levels equal the oracle's, its parents form a BFS tree, and
+    its stats are its own."""
     import torch
     rp, ci, srcs, keys = rmat16
     d = Dev(rp, ci, relabel=relabel)
     try:
         k = 7  # odd: both slots, the last one used once more
         S = np.ascontiguousarray(srcs[:k])
-        if pinned:
+        if where == "pinned":
             L = torch.full((k * d.n,), -7, dtype=torch.int32, pin_memory=True)
             P = torch.full((k * d.n,), -7, dtype=torch.int32, pin_memory=True) if parents else None
+        elif where == "device":
+            L = torch.full((k * d.n,), -7, dtype=torch.int32, device="cuda")
+            P = torch.full((k * d.n,), -7, dtype=torch.int32, device="cuda") if parents else None
         else:
             L = np.full(k * d.n, -7, np.int32)
             P = np.full(k * d.n, -7, np.int32) if parents else None
         st = (B.bfs_stats * k)()
         B.bfs_run_batch(d.g, S, k, L, P, st)
+        if where == "device":
+            L, P = L.cpu(), (P.cpu() if parents else None)
         L = np.asarray(L).reshape(k, d.n)
         orc = oracle.Oracle(rp, ci)
         for i, s in enumerate(S):
