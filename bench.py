@@ -111,8 +111,10 @@ def gather_peak(torch, dev):
     """Measured rate of isolated 4-byte loads at random addresses: torch's
     gather kernel reading an int32 table of 16 MiB (L2-resident, like the
     level array the explore tests) and of 1 GiB (HBM), with 2^27 random
-    indices each; the higher rate, in loads (sectors) per second.  This is
-    the ceiling of a kernel whose every test is one scattered load."""
+    indices each; the higher rate, in loads (sectors) per second.  A
+    reference rate for a kernel whose every test is one scattered load, not
+    a hard ceiling: the gather also streams 12 B of index and output per
+    load, and the level step's biggest level runs above it."""
     best = 0.0
     g = torch.Generator(device=dev).manual_seed(7)
     out = torch.empty(1 << 27, dtype=torch.int32, device=dev)
