@@ -370,6 +370,8 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.col_idx = g->d_col_idx;
   p.level = level;
   p.parent = parent;
+  // a renumbered graph's outputs always pass through k_finalize
+  p.parent_lazy = g->relabel ? 1 : 0;
   for (int b = 0; b < 2; ++b) {
     p.F[b] = g->d_F[b];
     p.RS[b] = g->d_RS[b];

@@ -109,6 +109,11 @@ struct Params {
   const int32_t* col_idx;  // padded: readable up to a multiple of 4 entries past nnz
   int32_t* level;
   int32_t* parent;
+  // 1: parent[] is not cleared at init (parent[s] = s only).  Allowed when
+  // nothing reads the parent of an unreached vertex: the dedup reads only
+  // vertices claimed in the level, and the outputs pass through
+  // finalize_outputs, which reads a parent only where the level is >= 0.
+  int32_t parent_lazy;
   int32_t* F[2];
   int32_t* RS[2];
   int32_t* EX[2];
@@ -1108,18 +1113,19 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
         if (o == 3) { lv.w = 0; pv.w = s; }
       }
       L4[i] = lv;
-      P4[i] = pv;
+      if (!p.parent_lazy) P4[i] = pv;
     }
     for (long long v = (n4 << 2) + tid; v < n; v += stride) {
       p.level[v] = v == s ? 0 : -1;
-      p.parent[v] = v == s ? s : -1;
+      if (!p.parent_lazy) p.parent[v] = v == s ? s : -1;
     }
   } else {
     for (long long v = tid; v < n; v += stride) {
       p.level[v] = v == s ? 0 : -1;
-      p.parent[v] = v == s ? s : -1;
+      if (!p.parent_lazy) p.parent[v] = v == s ? s : -1;
     }
   }
+  if (p.parent_lazy && tid == 0) p.parent[s] = s;
   for (long long i = tid; i < p.max_chunks; i += stride) p.status[i].word = 0ull;
   for (long long i = tid; i < ((ctas + 3) & ~3); i += stride) p.bar_arrive[i] = 0;
   for (long long i = tid; i < (p.hub_n >> 5); i += stride) p.hub_bits[i] = 0u;
@@ -1151,10 +1157,12 @@ __device__ __forceinline__ void finalize_outputs(int32_t n, const int32_t* inv, 
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     const int i = __ldg(inv + v);
-    level_out[v] = level[i];
+    const int lv = level[i];
+    level_out[v] = lv;
     if (parent_out) {
+      // an unreached vertex's parent entry may never have been written
       const int q = parent[i];
-      parent_out[v] = q >= 0 ? __ldg(perm + q) : -1;
+      parent_out[v] = lv >= 0 ? __ldg(perm + q) : -1;
     }
   }
 }
