@@ -414,7 +414,9 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
 static int enqueue_traversal(bfs_graph* g, const Params& p, cudaEvent_t* ev) {
   const bool timed = ev != nullptr;
   if (timed) CUDA_TRY(cudaEventRecord(ev[0], g->stream));
-  const int igrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n / 4 + 255) / 256)));
+  // one 1024-thread block per SM (k_init holds the whole parameter block in
+  // registers, so a second one does not fit), grid-stride over the arrays
+  const int igrid = std::max(1, std::min(g->sms, (int)(((long long)g->n / 4 + kThreads - 1) / kThreads)));
   k_init<<<igrid, kThreads, 0, g->stream>>>(p, g->ctas);
   CUDA_TRY(cudaGetLastError());
   ++g->launches;
@@ -1050,7 +1052,7 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   p.small_edges = 256 * 32;
 
   // k_init clears the look-back and barrier state left by the previous call
-  const int igrid = std::max(1, std::min(d->sms * 8, (int)(((long long)n / 4 + 255) / 256)));
+  const int igrid = std::max(1, std::min(d->sms, (int)(((long long)n / 4 + kThreads - 1) / kThreads)));
   k_init<<<igrid, kThreads, 0, stream>>>(p, d->ctas);
   CUDA_TRY(cudaGetLastError());
   void* args[] = {&p};
