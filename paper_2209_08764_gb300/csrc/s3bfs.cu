@@ -33,6 +33,12 @@ int s3bfs_host_relabel(int32_t n, const int32_t* rp, const int32_t* ci, bool sor
 // dynamic shared memory of the level loop: the visited bits
 static size_t loop_smem(int hub_n) { return (size_t)hub_n / 8; }
 
+// A graph that is not renumbered gets a visited bit for every vertex up to
+// this size (128 KB of shared memory) when its traversals are top-down only.
+// Bottom-up levels test level[] through L1, which the larger bitmap would
+// shrink, so with them the limit stays kHubMax.
+constexpr int kBitsAllMax = 1 << 20;
+
 // the level loop for a CTA shape; DO: with bottom-up levels (a separate
 // kernel, so that the top-down loop carries no trace of them)
 static const void* level_loop_fn(int wpc, bool DO) {
@@ -183,7 +189,8 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     if ((flags & BFS_SYMMETRIC) && !s3bfs_host_is_symmetric(n, rp, ci))
       return fail(BFS_E_INVAL, "BFS_SYMMETRIC: an edge lacks its reverse");
   }
-  // shared-memory visited bits: every vertex when n is small, else the
+  // shared-memory visited bits: every vertex when n is small (kHubMax; up to
+  // kBitsAllMax for a graph that is not skewed, top-down only), else the
   // kHubMax highest-degree vertices after a degree-descending renumbering,
   // if they hold at least half of the edge endpoints (skewed graphs)
   bool csr_on_host = !dev_in || !h_rp.empty();  // rp / ci are host arrays
@@ -231,6 +238,8 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
         CUDA_TRY(cudaMemcpyAsync(g->d_inv, g->h_inv.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
                                  g->stream));
         CUDA_TRY(cudaStreamSynchronize(g->stream));
+      } else if (relabel_opt == 0 && !g->direction && n <= kBitsAllMax) {
+        g->hub_n = (n + 127) / 128 * 128;
       }
     }
   }
@@ -267,7 +276,8 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   // persistent grid: every CTA that fits next to the shared-memory bits
   const void* loop_fn = level_loop_fn(g->wpc, g->direction != 0);
   // the attribute is per kernel, shared by every graph: set it to the largest size any graph uses
-  CUDA_TRY(cudaFuncSetAttribute(loop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem(kHubMax)));
+  CUDA_TRY(cudaFuncSetAttribute(loop_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)loop_smem(std::max(kHubMax, kBitsAllMax))));
   int per_sm = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, loop_fn, g->wpc * kWarp, loop_smem(g->hub_n)));
   if (per_sm < 1) return fail(BFS_E_CUDA, "level-loop kernel cannot be resident (occupancy 0)");
