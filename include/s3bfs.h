@@ -63,9 +63,11 @@ typedef struct bfs_opts {
   int32_t relabel;          /* visited bits in shared memory: 0 (default) = for every
                                vertex when n <= 2^18, else for the 2^18 highest-degree
                                vertices after a degree-descending renumbering, when
-                               they hold >= half of the edge endpoints; 1 = always
-                               renumber; -1 = neither.  Renumbering is internal:
-                               inputs and outputs keep the caller's vertex ids */
+                               they hold >= half of the edge endpoints, else (graph
+                               not skewed, direction = 0) for every vertex when
+                               n <= 2^20; 1 = always renumber; -1 = neither.
+                               Renumbering is internal: inputs and outputs keep the
+                               caller's vertex ids */
   int32_t batch_bitmask;    /* bfs_run_batch on a BFS_SYMMETRIC graph: 0 (default) =
                                groups of up to 64 sources share one traversal with a
                                64-bit mask per vertex; -1 = one traversal per source */
