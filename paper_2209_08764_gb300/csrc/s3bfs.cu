@@ -800,13 +800,15 @@ static int pipe_setup(bfs_graph* g, bool host) {
     }
   }
   if (g->pipe_ready) return BFS_OK;
+  // each handle is created once (a call that failed half-way resumes here)
   for (int s = 0; s < 2; ++s) {
-    for (auto& e : g->slot_ev[s]) CUDA_TRY(cudaEventCreate(&e));
-    CUDA_TRY(cudaEventCreateWithFlags(&g->slot_ready[s], cudaEventDisableTiming));
-    CUDA_TRY(cudaEventCreateWithFlags(&g->slot_copied[s], cudaEventDisableTiming));
+    for (auto& e : g->slot_ev[s])
+      if (!e) CUDA_TRY(cudaEventCreate(&e));
+    if (!g->slot_ready[s]) CUDA_TRY(cudaEventCreateWithFlags(&g->slot_ready[s], cudaEventDisableTiming));
+    if (!g->slot_copied[s]) CUDA_TRY(cudaEventCreateWithFlags(&g->slot_copied[s], cudaEventDisableTiming));
   }
-  CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
-  if (cudaHostAlloc((void**)&g->h_slot_st, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) {
+  if (!g->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+  if (!g->h_slot_st && cudaHostAlloc((void**)&g->h_slot_st, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     g->h_slot_st = nullptr;
     return fail(BFS_E_NOMEM, "pinned host allocation failed");
