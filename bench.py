@@ -872,13 +872,17 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                        for r, b in zip(recs.tolist(), bytes_loop.tolist())], f)
     line = None
     if rank == 0:
+        # config: the workload alone (the reference arm prints the same);
+        # method: how this arm traverses it
         config = config_of(args.workload, w, rp, ci)
-        config["direction"] = "direction-optimising (alpha 15, beta 18)" if direction else "top-down (S3BFS level step)"
-        config["options"] = {f: getattr(opts, f) for f, _ in opts._fields_ if getattr(opts, f)}
+        method = {"direction": "direction-optimising (alpha 15, beta 18)" if direction
+                  else "top-down (S3BFS level step)",
+                  "options": {f: getattr(opts, f) for f, _ in opts._fields_ if getattr(opts, f)},
+                  "step": "one bfs_run_batch over the sources (single-source traversals queued back to back)"}
         line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": config, "roofline": roofline,
+                "config": config, "method": method, "roofline": roofline,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "harmonic_mean_gteps_level_step": float(hmean),
                 "ms_level_step_median": float(np.median(ms_loop)),
