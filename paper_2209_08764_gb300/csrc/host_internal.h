@@ -72,15 +72,17 @@ struct bfs_graph {
   int32_t* d_groups = nullptr;  // vs[64], src_int[64], src_out[64]
   unsigned long long* d_masks = nullptr;
   int32_t *d_stage_level = nullptr, *d_stage_parent = nullptr;  // 64 x n, for host outputs
-  // batches of single-source traversals queued back to back: per slot (i & 1)
-  // events and a pinned state block; with host outputs also a device staging
-  // pair (level, parent) whose copy to the host overlaps the next traversal
+  // batches of single-source traversals queued back to back: a ring of
+  // kQueueDepth slots (events, pinned state block) lets the host run that many
+  // traversals ahead; with host outputs also two device staging pairs (level,
+  // parent) whose copies to the host overlap the next traversal
+  static constexpr int kQueueDepth = 8;
   bool pipe_ready = false;
   cudaStream_t copy_stream = nullptr;
   int32_t *d_slot_level[2] = {nullptr, nullptr}, *d_slot_parent[2] = {nullptr, nullptr};
-  cudaEvent_t slot_ev[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-  cudaEvent_t slot_ready[2] = {nullptr, nullptr}, slot_copied[2] = {nullptr, nullptr};
-  DevState* h_slot_st = nullptr;  // pinned [2]
+  cudaEvent_t slot_ev[kQueueDepth][3] = {};
+  cudaEvent_t slot_ready[kQueueDepth] = {}, slot_copied[kQueueDepth] = {};
+  DevState* h_slot_st = nullptr;  // pinned [kQueueDepth]
 };
 
 // last error text of this host thread (bfs_last_error) and its setter

@@ -103,7 +103,7 @@ extern "C" void bfs_destroy(bfs_graph* g) {
     cudaStreamSynchronize(g->copy_stream);
     cudaStreamDestroy(g->copy_stream);
   }
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < bfs_graph::kQueueDepth; ++s) {
     for (auto& e : g->slot_ev[s])
       if (e) cudaEventDestroy(e);
     if (g->slot_ready[s]) cudaEventDestroy(g->slot_ready[s]);
@@ -781,15 +781,16 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
 
 // ---- batches of single-source traversals, queued back to back -----------
 //
-// Traversal i runs on the graph's stream, its device state block is copied
-// to pinned slot i & 1 and an event marks it done; the host checks traversal
-// i - 1 (error, stats) only after it has queued traversal i, so the GPU does
-// not wait for the host between traversals.  Device outputs are written in
-// place (through k_finalize on a renumbered graph).  Host outputs go through
-// device staging slot i & 1: a second stream copies the slot to the caller's
-// buffers while traversal i + 1 runs, and traversal i + 2 waits for that copy
-// before it reuses the slot.  Copies into pageable host memory are correct
-// but do not overlap.
+// Traversal i runs on the graph's stream and uses ring slot i % D (D =
+// kQueueDepth): its timing events, a pinned copy of its device state block
+// and an event that marks it done.  The host queues up to D traversals ahead
+// and checks traversal i - D (error, stats) before it reuses that slot, so a
+// host that falls behind for a while does not leave the GPU idle.  Device
+// outputs are written in place (through k_finalize on a renumbered graph).
+// Host outputs go through device staging pair i & 1: a second stream copies
+// it to the caller's buffers while traversal i + 1 runs, and traversal i + 2
+// waits for that copy on the device before it reuses the pair.  Copies into
+// pageable host memory are correct but do not overlap.
 
 static int pipe_setup(bfs_graph* g, bool host) {
   int rc;
@@ -801,14 +802,16 @@ static int pipe_setup(bfs_graph* g, bool host) {
   }
   if (g->pipe_ready) return BFS_OK;
   // each handle is created once (a call that failed half-way resumes here)
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < bfs_graph::kQueueDepth; ++s) {
     for (auto& e : g->slot_ev[s])
       if (!e) CUDA_TRY(cudaEventCreate(&e));
     if (!g->slot_ready[s]) CUDA_TRY(cudaEventCreateWithFlags(&g->slot_ready[s], cudaEventDisableTiming));
     if (!g->slot_copied[s]) CUDA_TRY(cudaEventCreateWithFlags(&g->slot_copied[s], cudaEventDisableTiming));
   }
   if (!g->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
-  if (!g->h_slot_st && cudaHostAlloc((void**)&g->h_slot_st, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) {
+  if (!g->h_slot_st &&
+      cudaHostAlloc((void**)&g->h_slot_st, bfs_graph::kQueueDepth * sizeof(DevState), cudaHostAllocDefault) !=
+          cudaSuccess) {
     cudaGetLastError();
     g->h_slot_st = nullptr;
     return fail(BFS_E_NOMEM, "pinned host allocation failed");
@@ -819,26 +822,35 @@ static int pipe_setup(bfs_graph* g, bool host) {
 
 static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int32_t* levels_out,
                                int32_t* parents_out, bfs_stats* stats, bool host) {
+  constexpr int D = bfs_graph::kQueueDepth;
   int rc = pipe_setup(g, host);
   if (rc != BFS_OK) return rc;
   const size_t n = (size_t)g->n;
-  int launches[2] = {0, 0};
+  int launches[D] = {};
   // wait for traversal i (and its copy), then check it
   auto finish = [&](int32_t i) -> int {
-    const int s = i & 1;
+    const int s = i % D;
     CUDA_TRY(cudaEventSynchronize(host ? g->slot_copied[s] : g->slot_ready[s]));
     const DevState& st = g->h_slot_st[s];
     int r = traversal_error(st, srcs[i]);
     if (r == BFS_OK && stats) r = traversal_stats(g, st, launches[s], g->slot_ev[s], stats + i);
     return r;
   };
-  int32_t failed = -1;
+  int32_t failed = -1, done = 0;  // traversals [0, done) are checked
   for (int32_t i = 0; i < k && rc == BFS_OK; ++i) {
-    const int s = i & 1;
-    if (host && i >= 2) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[s], 0));
+    if (i >= D) {
+      // ring slot i % D is free once traversal i - D is checked
+      if ((rc = finish(done)) != BFS_OK) {
+        failed = done;
+        break;
+      }
+      ++done;
+    }
+    const int s = i % D, b = i & 1;
+    if (host && i >= 2) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[(i - 2) % D], 0));
     // this traversal's outputs on the device, and its working arrays
-    int32_t* lo = host ? g->d_slot_level[s] : levels_out + (size_t)i * n;
-    int32_t* po = parents_out ? (host ? g->d_slot_parent[s] : parents_out + (size_t)i * n) : nullptr;
+    int32_t* lo = host ? g->d_slot_level[b] : levels_out + (size_t)i * n;
+    int32_t* po = parents_out ? (host ? g->d_slot_parent[b] : parents_out + (size_t)i * n) : nullptr;
     int32_t* lw = g->relabel ? g->d_level : lo;
     int32_t* pw = (g->relabel || !po) ? g->d_parent : po;
     const Params p = make_params(g, g->relabel ? g->h_inv[srcs[i]] : srcs[i], lw, pw);
@@ -866,9 +878,11 @@ static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int
                                  g->copy_stream));
       CUDA_TRY(cudaEventRecord(g->slot_copied[s], g->copy_stream));
     }
-    if (i >= 1 && (rc = finish(i - 1)) != BFS_OK) failed = i - 1;
   }
-  if (rc == BFS_OK && k >= 1 && (rc = finish(k - 1)) != BFS_OK) failed = k - 1;
+  while (rc == BFS_OK && done < k) {
+    if ((rc = finish(done)) != BFS_OK) failed = done;
+    ++done;
+  }
   if (rc != BFS_OK) {
     // nothing of this call stays in flight
     cudaStreamSynchronize(g->stream);
