@@ -48,3 +48,25 @@ def test_cpulist_parsing():
     assert bench.parse_cpulist("0-3,8,10-11") == [0, 1, 2, 3, 8, 10, 11]
     assert bench.parse_cpulist("72-143\n") == list(range(72, 144))
     assert bench.parse_cpulist("") == []
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference (the oracle on one host core) prints one
+    JSON line with the contract's keys, on the same config as the GPU arm."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "rmat16", "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=300,
+                         cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([x for x in out.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["unit"] == "GTEPS" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 1
+    w = bench.WORKLOADS["rmat16"]
+    assert line["config"]["workload"] == "rmat16" and line["config"]["sources"] == w["sources"]
+    assert set(line["config"]) >= {"workload", "n", "nnz", "sources", "l2", "parallelism"}
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
