@@ -274,6 +274,19 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def graph500_edges(deg, level, st) -> int:
+    """Traversed edges of one traversal, Graph500 count for a symmetric CSR:
+    half the summed degree of the reached vertices.  The library sums the
+    same degrees on the device (``edges_scanned`` = sum of e_l over the
+    levels); the two counts must agree, so the GPU arm's numerator is the
+    definition the tests pin on the CPU side."""
+    host = int(deg[np.asarray(level) >= 0].sum() // 2)
+    dev = int(st.edges_scanned) // 2
+    if host != dev:
+        raise RuntimeError(f"traversed-edge counts disagree: degree sum {host}, library {dev}")
+    return dev
+
+
 def config_of(name, w, rp, ci):
     c = {"workload": name, "n": int(len(rp) - 1), "nnz": int(len(ci)), "sources": int(w["sources"])}
     c.update({k: v for k, v in w.items() if k not in ("kind", "sources")})
@@ -364,7 +377,7 @@ def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     B.bfs_run_batch(g, S, k, L, P, st)
     deg = np.diff(rp.astype(np.int64))
     Lh = L.cpu().numpy().reshape(k, n)
-    teps = [int(deg[Lh[i] >= 0].sum() // 2) for i in range(k)]
+    teps = [graph500_edges(deg, Lh[i], st[i]) for i in range(k)]
     edges_per_step = sum(teps)
     levels = max(st[i].num_levels for i in range(k))
     work = st[0].work_edges
@@ -764,7 +777,7 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     teps_edges, src_bytes, first_rows, bu_levels = [], [], None, []
     for s in srcs:
         B.bfs_run(g, int(s), level, parent, st2)
-        teps_edges.append(int(deg[(level >= 0).cpu().numpy()].sum() // 2))
+        teps_edges.append(graph500_edges(deg, level.cpu().numpy(), st2))
         L = min(st2.num_levels, cap)
         rows = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS).copy()
         src_bytes.append(level_bytes(n, rows) if L == st2.num_levels else np.nan)

@@ -17,6 +17,9 @@ Contents
 ``s3bfs_fig1``       Fig. 1 itself, step by step in the paper's order and
                      notation (numpy per step), for per-level quantities:
                      n_l, e_l, P_l, the start points, candidates and Sizes.
+``traversed_edges``  Graph500 traversed-edge count of one traversal (half the
+                     degree sum of the reached vertices), the numerator of
+                     every GTEPS figure.
 ``start_points_scatter`` / ``start_points_bsearch``
                      Find-StartExpPoint (Fig. 1) in the paper's range-
                      scatter form (Analysis, last paragraph) and in the binary

@@ -102,6 +102,8 @@ def check_against_oracle(dev, src, orc=None, keys=None, per_level=True, grain=64
     assert st.num_levels == len(n_l)
     assert st.reached == int(n_l.sum())
     assert st.edges_scanned == int(e_l.sum())
+    # the GTEPS numerator: the library's count equals the pinned oracle count
+    assert st.edges_scanned // 2 == oracle.traversed_edges(dev.rp, want)
     dirs = expected_directions(dev.n, len(dev.ci), n_l, e_l, dev.direction, dev.alpha, dev.beta, dev.gamma,
                                dev.n_live)
     bu = dirs == 1

@@ -449,3 +449,88 @@ def test_fig1_star_closed_form():
         assert r["starts"].tolist() == [[0, t * C] for t in range(T)]
         # second pass: every leaf has one edge back to the centre
         assert levels[1]["e_l"] == k and levels[1]["candidates"] == 0
+
+
+# ---------------------------------------------------------------------------
+# traversed_edges: the Graph500 edge count behind every GTEPS figure
+# ---------------------------------------------------------------------------
+
+def _disjoint(a, b):
+    """Disjoint union of two CSR graphs; b's vertices follow a's."""
+    (ra, ca), (rb, cb) = a, b
+    na = len(ra) - 1
+    rp = np.concatenate([ra, rb[1:] + ra[-1]]).astype(np.int32)
+    ci = np.concatenate([ca, cb + na]).astype(np.int32)
+    return rp, ci
+
+
+def pins_traversed_edges(te):
+    """Closed forms for the undirected edges inside the source's component,
+    then brute force on every simple graph with n <= 5 (the count of listed
+    vertex pairs whose two ends lie in the source's component)."""
+    def count(rp, ci, s):
+        lv, _ = oracle.bfs(rp, ci, s)
+        return te(rp, lv)
+    for n in (1, 2, 7, 40):
+        rp, ci = path(n)
+        for s in {0, n // 2, n - 1}:
+            assert count(rp, ci, s) == n - 1, ("path", n, s)
+    for k in (1, 3, 12):
+        rp, ci = star(k)
+        assert count(rp, ci, 0) == k and count(rp, ci, k) == k, ("star", k)
+    for n in (2, 5, 9):
+        rp, ci = complete(n)
+        assert count(rp, ci, n - 1) == n * (n - 1) // 2, ("K_n", n)
+    for a, b in ((1, 4), (3, 5)):
+        rp, ci = complete_bipartite(a, b)
+        assert count(rp, ci, 0) == a * b and count(rp, ci, a) == a * b, ("K_ab", a, b)
+    for n in (3, 10):
+        rp, ci = cycle(n)
+        assert count(rp, ci, 1) == n, ("cycle", n)
+    rp, ci = graphgen.grid(6, 9, 0.0)
+    assert count(rp, ci, 0) == 6 * 8 + 9 * 5, "grid"
+    rp, ci = binary_tree(5)
+    assert count(rp, ci, 0) == (1 << 5) - 2, "binary tree"
+    # disjoint union: only the source's component counts
+    rp, ci = _disjoint(path(4), complete(5))
+    assert count(rp, ci, 1) == 3 and count(rp, ci, 6) == 10, "disjoint union"
+    # an isolated source traverses nothing
+    rp, ci = _disjoint(graphgen.from_edges(1, []), complete(4))
+    assert count(rp, ci, 0) == 0, "isolated source"
+    for n in range(1, 6):
+        A = _all_graphs(n)
+        for g in range(len(A)):
+            rp, ci = _csr_of(A[g])
+            _, comp = connected_components(sp.csr_matrix(A[g]), directed=False)
+            iu, ju = np.nonzero(np.triu(A[g], 1))
+            for s in range(n):
+                want = int(np.sum(comp[iu] == comp[s]))
+                got = count(rp, ci, s)
+                if got != want:
+                    raise AssertionError(f"traversed edges n={n} graph={g} s={s}: {got} != {want}")
+
+
+def test_traversed_edges_pins():
+    pins_traversed_edges(oracle.traversed_edges)
+
+
+TE_MUTANTS = {
+    "no halving": ("].sum() // 2)", "].sum())"),
+    "every vertex": ("deg[np.asarray(level) >= 0]", "deg"),
+    "source left out": ("np.asarray(level) >= 0", "np.asarray(level) > 0"),
+    "row ends, not degrees": ("np.diff(np.asarray(row_ptr, np.int64))", "np.asarray(row_ptr, np.int64)[1:]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TE_MUTANTS))
+def test_traversed_edges_pins_catch_planted_mistake(name):
+    import inspect
+    import textwrap
+
+    old, new = TE_MUTANTS[name]
+    src = textwrap.dedent(inspect.getsource(oracle.traversed_edges))
+    assert old in src, name
+    ns = {"np": np}
+    exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), ns)
+    with pytest.raises(AssertionError):
+        pins_traversed_edges(ns["traversed_edges"])
