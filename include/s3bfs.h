@@ -29,7 +29,7 @@ extern "C" {
 #define BFS_OK 0
 #define BFS_E_INVAL (-1)      /* bad argument: n, nnz, CSR contents, src, k, NULL pointer */
 #define BFS_E_MULTIGRAPH (-2) /* a row repeats a neighbour (the owner-as-parent dedup needs a simple graph) */
-#define BFS_E_NOMEM (-3)      /* device or pinned-host allocation failed, or the create-time memory cap */
+#define BFS_E_NOMEM (-3)      /* device or pinned-host allocation failed, or bfs_opts.max_device_bytes reached */
 #define BFS_E_CUDA (-4)       /* a CUDA runtime call or kernel launch failed; see bfs_last_error() */
 #define BFS_E_TIMEOUT (-5)    /* a device-side wait (grid barrier or scan look-back) hit its limit */
 
@@ -100,6 +100,12 @@ typedef struct bfs_opts {
                                the unvisited vertices of degree > 0 (on a GPU a
                                bottom-up test costs about what a top-down one does);
                                0 = 2, -1 = no such test (Beamer's rule alone) */
+  int32_t reserved;         /* must be 0 */
+  int64_t max_device_bytes; /* cap on the device memory this handle allocates, at create
+                               time and later (the bitmask-batch and queued-batch buffers
+                               are allocated at their first use); an allocation that
+                               would pass it fails with BFS_E_NOMEM and the call
+                               allocates nothing more.  0 = no cap */
 } bfs_opts;
 
 /* Per-level record written to bfs_stats.per_level, BFS_LEVEL_FIELDS int32 each. */
@@ -229,6 +235,12 @@ const char *bfs_last_error(void);
  * any output pointer may be NULL. */
 int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, int32_t *warps);
 
+/* bfs_graph_device_bytes -- device memory the graph currently holds (what
+ * bfs_opts.max_device_bytes caps), in bytes; -1 if g is NULL.  Buffers that
+ * bitmask batches and queued batches allocate at their first use count from
+ * then on. */
+int64_t bfs_graph_device_bytes(const bfs_graph *g);
+
 /*
  * bfs_run_csr_noalloc -- one traversal that allocates no memory at all.
  *
@@ -255,8 +267,10 @@ int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, 
  *
  * Every call, from any thread or stream, shares that one array, which keeps
  * the last call's contents; each call clears the state that must start at
- * zero.  Calls that overlap on the GPU (different streams or host threads on
- * the same device) race on the array and give wrong results: serialise them.
+ * zero.  Calls that overlapped on the GPU would race on the array and give
+ * wrong results, so the library holds a per-device lock for the whole of
+ * each call (which returns only once its traversal is done): calls from
+ * different host threads on one device run one after another.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and the grid size; make that first call before any
  * stream capture.

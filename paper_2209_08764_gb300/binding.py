@@ -31,7 +31,7 @@ BFS_DEBUG_STALL_BARRIER = 1
 BFS_LEVEL_FIELDS = 9
 
 EXPORTS = ("bfs_create_csr", "bfs_run", "bfs_run_batch", "bfs_destroy", "bfs_strerror", "bfs_last_error",
-           "bfs_graph_info", "bfs_run_csr_noalloc", "bfs_server_create", "bfs_server_submit", "bfs_server_poll",
+           "bfs_graph_info", "bfs_graph_device_bytes", "bfs_run_csr_noalloc", "bfs_server_create", "bfs_server_submit", "bfs_server_poll",
            "bfs_server_pending", "bfs_server_destroy")
 
 
@@ -51,6 +51,8 @@ class bfs_opts(ctypes.Structure):
         ("do_alpha", ctypes.c_int32),
         ("do_beta", ctypes.c_int32),
         ("do_gamma", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("max_device_bytes", ctypes.c_int64),
     ]
 
 
@@ -136,6 +138,8 @@ def load():
     lib.bfs_graph_info.restype = ctypes.c_int
     lib.bfs_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i32)]
+    lib.bfs_graph_device_bytes.restype = ctypes.c_int64
+    lib.bfs_graph_device_bytes.argtypes = [vp]
     lib.bfs_run_csr_noalloc.restype = ctypes.c_int
     lib.bfs_run_csr_noalloc.argtypes = [i32, i32, i32p, i32p, i32, i32p, i32p, vp]
     lib.bfs_server_create.restype = ctypes.c_int
@@ -215,6 +219,10 @@ def bfs_strerror(code: int) -> str:
 
 def bfs_last_error() -> str:
     return load().bfs_last_error().decode()
+
+
+def bfs_graph_device_bytes(g: int) -> int:
+    return int(load().bfs_graph_device_bytes(g))
 
 
 def bfs_graph_info(g: int) -> dict:

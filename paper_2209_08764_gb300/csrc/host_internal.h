@@ -58,6 +58,9 @@ struct bfs_graph {
   int32_t* h_ctrl = nullptr; // pinned, launch-per-phase mode
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
+  size_t dev_bytes = 0;  // device memory allocated through dalloc
+  size_t dev_cap = 0;    // bfs_opts.max_device_bytes (0 = no cap)
+  bool ms_arrive_grown = false;  // bitmask batches widened the barrier's arrival words
   // multi-source (bitmask) batches, allocated at the first batch
   bool symmetric = false;
   int batch_bitmask = 0;
@@ -100,12 +103,16 @@ template <class T>
 inline int dalloc(bfs_graph* g, T** p, size_t count) {
   void* q = nullptr;
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (g->dev_cap && g->dev_bytes + bytes > g->dev_cap)
+    return fail(BFS_E_NOMEM, "device memory cap: %zu bytes allocated, %zu more would pass max_device_bytes = %zu",
+                g->dev_bytes, bytes, g->dev_cap);
   cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(BFS_E_NOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
   g->allocs.push_back(q);
+  g->dev_bytes += bytes;
   *p = static_cast<T*>(q);
   return BFS_OK;
 }

@@ -55,7 +55,7 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
     e_begin = (int)min(eb, (long long)e_l);
     const int e_end = (int)min(eb + C_l, (long long)e_l);
     work = e_end - e_begin;
-    if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
+    if (e_begin < e_end) cnt = explore_chunk<W>(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
   }
   if (GRID) {
     if (!grid_sync(p, ++*bar)) return false;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(W * kWarp) k_explore(Params p, int l, int n_l,
   const int e_begin = (int)min(eb, (long long)e_l);
   const int e_end = (int)min(eb + C_l, (long long)e_l);
   int cnt = 0;
-  if (e_begin < e_end) cnt = explore_chunk(p, l, l & 1, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
+  if (e_begin < e_end) cnt = explore_chunk<W>(p, l, l & 1, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
   if ((threadIdx.x & (kWarp - 1)) == 0) p.cand_cnt[gw] = cnt;
 }
 

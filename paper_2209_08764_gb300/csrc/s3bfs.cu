@@ -114,6 +114,8 @@ extern "C" void bfs_destroy(bfs_graph* g) {
   delete g;
 }
 
+extern "C" int64_t bfs_graph_device_bytes(const bfs_graph* g) { return g ? (int64_t)g->dev_bytes : -1; }
+
 extern "C" int bfs_graph_info(const bfs_graph* g, int32_t* n, int32_t* nnz, int32_t* ctas, int32_t* warps) {
   if (!g) return fail(BFS_E_INVAL, "graph is NULL");
   if (n) *n = g->n;
@@ -132,6 +134,9 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device));
   if (opts) {
     if (opts->chunk_edges > 0) g->grain = opts->chunk_edges;
+    if (opts->reserved != 0) return fail(BFS_E_INVAL, "bfs_opts.reserved must be 0");
+    if (opts->max_device_bytes < 0) return fail(BFS_E_INVAL, "max_device_bytes must be >= 0");
+    g->dev_cap = (size_t)opts->max_device_bytes;
     if (opts->persistent < 0) g->persistent = 0;
     g->work_insensitive = opts->work_insensitive != 0;
     if (opts->spin_limit_ms > 0) g->spin_ns = (long long)opts->spin_limit_ms * 1000000ll;
@@ -612,11 +617,13 @@ extern "C" int bfs_run(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* p
 
 static int ms_setup(bfs_graph* g) {
   if (g->ms_ready) return BFS_OK;
+  // every buffer is allocated once: a call that failed half-way (memory cap)
+  // resumes here without leaking what it got
   int rc;
   const size_t n = (size_t)g->n;
-  if ((rc = dalloc(g, &g->d_seen, n)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_fr[0], n)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_fr[1], n)) != BFS_OK) return rc;
+  if (!g->d_seen && (rc = dalloc(g, &g->d_seen, n)) != BFS_OK) return rc;
+  if (!g->d_fr[0] && (rc = dalloc(g, &g->d_fr[0], n)) != BFS_OK) return rc;
+  if (!g->d_fr[1] && (rc = dalloc(g, &g->d_fr[1], n)) != BFS_OK) return rc;
   // heavy vertices (internal ids), from a host copy of row_ptr
   std::vector<int32_t> rp(n + 1), heavy, huge;
   CUDA_TRY(cudaMemcpy(rp.data(), g->d_row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
@@ -629,8 +636,8 @@ static int ms_setup(bfs_graph* g) {
   }
   g->n_heavy = (int32_t)heavy.size();
   g->n_huge = (int32_t)huge.size();
-  if ((rc = dalloc(g, &g->d_heavy, std::max<size_t>(heavy.size(), 1))) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_huge, std::max<size_t>(huge.size(), 1))) != BFS_OK) return rc;
+  if (!g->d_heavy && (rc = dalloc(g, &g->d_heavy, std::max<size_t>(heavy.size(), 1))) != BFS_OK) return rc;
+  if (!g->d_huge && (rc = dalloc(g, &g->d_huge, std::max<size_t>(huge.size(), 1))) != BFS_OK) return rc;
   if (!heavy.empty())
     CUDA_TRY(cudaMemcpy(g->d_heavy, heavy.data(), sizeof(int32_t) * heavy.size(), cudaMemcpyHostToDevice));
   if (!huge.empty())
@@ -640,15 +647,16 @@ static int ms_setup(bfs_graph* g) {
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_msbfs, kThreads, kMsParentSmem));
   if (per_sm < 1) return fail(BFS_E_CUDA, "multi-source kernel cannot be resident (occupancy 0)");
   g->ms_ctas = per_sm * g->sms;
-  if ((rc = dalloc(g, &g->d_block_or, 2 * (size_t)g->ms_ctas)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_level_bits, (size_t)g->lvl_cap)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_counts, (size_t)g->ms_ctas * 128)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_block_edges, (size_t)g->ms_ctas)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_groups, 3 * 64)) != BFS_OK) return rc;
-  if ((rc = dalloc(g, &g->d_masks, 64)) != BFS_OK) return rc;
+  if (!g->d_block_or && (rc = dalloc(g, &g->d_block_or, 2 * (size_t)g->ms_ctas)) != BFS_OK) return rc;
+  if (!g->d_level_bits && (rc = dalloc(g, &g->d_level_bits, (size_t)g->lvl_cap)) != BFS_OK) return rc;
+  if (!g->d_counts && (rc = dalloc(g, &g->d_counts, (size_t)g->ms_ctas * 128)) != BFS_OK) return rc;
+  if (!g->d_block_edges && (rc = dalloc(g, &g->d_block_edges, (size_t)g->ms_ctas)) != BFS_OK) return rc;
+  if (!g->d_groups && (rc = dalloc(g, &g->d_groups, 3 * 64)) != BFS_OK) return rc;
+  if (!g->d_masks && (rc = dalloc(g, &g->d_masks, 64)) != BFS_OK) return rc;
   if (g->ctas < g->ms_ctas) {
     // the barrier's arrival words must cover this grid too
-    if ((rc = dalloc(g, &g->d_arrive, (size_t)(g->ms_ctas + 3) / 4 * 4)) != BFS_OK) return rc;
+    if (!g->ms_arrive_grown && (rc = dalloc(g, &g->d_arrive, (size_t)(g->ms_ctas + 3) / 4 * 4)) != BFS_OK) return rc;
+    g->ms_arrive_grown = true;
   }
   g->ms_ready = true;
   return BFS_OK;
@@ -984,6 +992,9 @@ struct NoAllocDevice {
 };
 static NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 static std::mutex g_noalloc_mu;
+// held for a whole call: calls from different host threads on one device
+// would otherwise overlap on the GPU and race on the shared array
+static std::mutex g_noalloc_call_mu[kNoAllocMaxDevices];
 
 // Per-device set-up, done by the first call on each device with that device
 // current: look up the scratch address and the persistent grid size.
@@ -1022,6 +1033,7 @@ extern "C" int bfs_run_csr_noalloc(int32_t n, int32_t nnz, const int32_t* row_pt
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(BFS_E_INVAL, "device %d beyond %d", dev, kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> call_lock(g_noalloc_call_mu[dev]);
   NoAllocDevice* d = nullptr;
   int rc = noalloc_setup(dev, &d);
   if (rc != BFS_OK) return rc;

@@ -403,10 +403,19 @@ __device__ __forceinline__ int emit(int2* out, int cnt, bool k, int v, int u, in
 #ifndef S3BFS_EXPLORE_QUAL
 #define S3BFS_EXPLORE_QUAL inline
 #endif
+#ifndef S3BFS_OWNER_REDUX
+#define S3BFS_OWNER_REDUX 1  // 1: quad owners by ballot + OR-reduction and shared records; 0: shuffle search
+#endif
+template <int W>  // warps per CTA
 __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par, int n_l, int e_l, int e_begin,
                                                 int e_end,
                              int2* out, const uint32_t* s_hub, int hub_lim) {
   const int lane = threadIdx.x & (kWarp - 1);
+#if S3BFS_OWNER_REDUX
+  __shared__ int4 s_rec[W][kWarp];
+  int4* rec = s_rec[threadIdx.x >> 5];
+  const unsigned lane_lt = (1u << lane) - 1u;
+#endif
   // (selects, not p.EX[par]: a runtime index into the parameter block would
   // copy it to local memory)
   const int* EX = par ? p.EX[1] : p.EX[0];
@@ -460,6 +469,15 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
     const int qend = warp_incl_scan(nq, lane);
     const int Q = __shfl_sync(kFull, qend, kWarp - 1);
     const int qoff = qend - nq;
+#if S3BFS_OWNER_REDUX
+    // The entries that own quads, packed by rank into the warp's shared
+    // records: quad q of the window lies at col_idx quad R.x + q and belongs
+    // to edges [R.y, R.z) of vertex R.w.
+    __syncwarp();
+    const unsigned nzm = __ballot_sync(kFull, nq > 0);
+    if (nq > 0) rec[__popc(nzm & lane_lt)] = make_int4(q0 - qoff, p0, p1, u);
+    __syncwarp();
+#endif
     // Load-balanced walk: round r hands quad r*32+lane to this lane; its owner
     // entry w is the first lane whose quad range ends after it.
     for (int base = 0; base < Q; base += kWarp * S3BFS_QPL) {
@@ -468,19 +486,35 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
 #pragma unroll
       for (int r = 0; r < S3BFS_QPL; ++r) {
         const int q = base + r * kWarp + lane;
+        const bool act = q < Q;
+#if S3BFS_OWNER_REDUX
+        // owner rank of quad q: the entries ending at or before the block
+        // start B, plus those ending inside (B, q] (one bit each: quad ranges
+        // of non-empty entries end at distinct positions)
+        const int B = base + r * kWarp;
+        const int wB = __popc(__ballot_sync(kFull, nq > 0 && qend <= B));
+        const unsigned endbit = (nq > 0 && qend > B && qend < B + kWarp) ? 1u << (qend - B - 1) : 0u;
+        const unsigned ends = __reduce_or_sync(kFull, endbit);
+        const int w = min(wB + __popc(ends & lane_lt), kWarp - 1);
+        const int4 R = rec[w];  // (a lane past Q may read a record this launch never wrote)
+        const int qa = R.x + q;
+        wp0[r] = R.y;
+        wp1[r] = act ? R.z : 0;  // no valid position on a lane past Q
+        wu[r] = R.w;
+#else
         int w = 0;
 #pragma unroll
         for (int s = 16; s >= 1; s >>= 1) {
           const int t = __shfl_sync(kFull, qend, w + s - 1);
           if (t <= q) w += s;
         }
-        const bool act = q < Q;
         const int wq0 = __shfl_sync(kFull, q0, w);
         const int wqoff = __shfl_sync(kFull, qoff, w);
         wp0[r] = __shfl_sync(kFull, p0, w);
         wp1[r] = __shfl_sync(kFull, p1, w);
         wu[r] = __shfl_sync(kFull, u, w);
         const int qa = wq0 + (q - wqoff);
+#endif
         c[r] = make_int4(0, 0, 0, 0);
         if (act) c[r] = ld_col4(col4 + qa, pol);
         pos[r] = act ? (qa << 2) : 0x7FFFFFF0;   // inactive: no position is valid

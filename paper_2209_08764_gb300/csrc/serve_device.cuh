@@ -121,7 +121,7 @@ __device__ void serve_local(const ServeParams& sp, SlotDev* sd) {
       e_begin = (int)min(eb, (long long)e_l);
       const int e_end = (int)min(eb + C_l, (long long)e_l);
       work = e_end - e_begin;
-      if (e_begin < e_end) cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
+      if (e_begin < e_end) cnt = explore_chunk<W>(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
     }
     __syncthreads();
     if (P_l == 0) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
         const int e_end = (int)min(eb + C_l, (long long)e_l);
         work = e_end - e_begin;
         if (e_begin < e_end)
-          cnt = explore_chunk(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
+          cnt = explore_chunk<W>(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
       }
     }
     if (!grid_sync(sp, ++bar)) break;

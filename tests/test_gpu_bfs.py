@@ -366,6 +366,42 @@ def test_bad_source_and_bad_csr():
     assert e.value.code == B.BFS_E_INVAL
 
 
+def test_device_memory_cap_gives_nomem():
+    """bfs_opts.max_device_bytes: create-time buffers beyond the cap fail with
+    BFS_E_NOMEM; a cap that exactly fits them works, and a later first-use
+    allocation beyond it (the bitmask-batch buffers) fails the same way while
+    the graph stays usable."""
+    import torch
+    rp, ci = graphgen.rmat(12, 16, seed=3)
+    n = len(rp) - 1
+    stream = torch.cuda.current_stream().cuda_stream
+    flags = B.BFS_VALIDATE | B.BFS_SYMMETRIC
+    g = B.bfs_create_csr(n, len(ci), rp, ci, flags, None, stream)
+    need = B.bfs_graph_device_bytes(g)
+    B.bfs_destroy(g)
+    assert need > 8 * n
+    with pytest.raises(B.BFSError) as e:
+        B.bfs_create_csr(n, len(ci), rp, ci, flags, make_opts(max_device_bytes=need - 1), stream)
+    assert e.value.code == B.BFS_E_NOMEM and "max_device_bytes" in str(e.value)
+    g = B.bfs_create_csr(n, len(ci), rp, ci, flags, make_opts(max_device_bytes=need), stream)
+    try:
+        assert B.bfs_graph_device_bytes(g) == need
+        srcs = np.ascontiguousarray(graphgen.sample_sources(rp, 4, seed=1), np.int32)
+        L = torch.empty(len(srcs) * n, dtype=torch.int32, device="cuda")
+        with pytest.raises(B.BFSError) as e:
+            B.bfs_run_batch(g, srcs, len(srcs), L, None, None)
+        assert e.value.code == B.BFS_E_NOMEM
+        assert B.bfs_graph_device_bytes(g) <= need
+        lv = torch.empty(n, dtype=torch.int32, device="cuda")
+        B.bfs_run(g, int(srcs[0]), lv, None, None)          # still usable
+        assert np.array_equal(lv.cpu().numpy(), oracle.bfs(rp, ci, int(srcs[0]))[0])
+    finally:
+        B.bfs_destroy(g)
+    with pytest.raises(B.BFSError) as e:
+        B.bfs_create_csr(n, len(ci), rp, ci, flags, make_opts(max_device_bytes=-5), stream)
+    assert e.value.code == B.BFS_E_INVAL
+
+
 def test_multigraph_rejected_or_deduplicated():
     rp = np.array([0, 3, 5, 6, 7], np.int32)      # row 0 lists 1 twice, row 1 has a self-loop
     ci = np.array([1, 2, 1, 0, 1, 0, 1], np.int32)

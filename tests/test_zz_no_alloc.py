@@ -1,4 +1,4 @@
-"""The allocation-free entry point, checked against bfs_run (GPU only).
+"""The allocation-free entry point, checked against the oracle and bfs_run (GPU only).
 
 bfs_run_csr_noalloc serves callers that must not allocate device memory while
 they traverse (code inside a framework whose caching allocator owns the GPU's
@@ -31,7 +31,8 @@ def _reference(rp, ci, srcs):
     """Levels (and a valid tree) from the allocating entry point bfs_run."""
     import torch
     n = len(rp) - 1
-    g = B.bfs_create_csr(n, len(ci), rp, ci, B.BFS_VALIDATE, None, torch.cuda.current_stream().cuda_stream)
+    g = B.bfs_create_csr(n, len(ci), rp, ci if len(ci) else None, B.BFS_VALIDATE, None,
+                         torch.cuda.current_stream().cuda_stream)
     out = []
     try:
         for s in srcs:
@@ -43,17 +44,25 @@ def _reference(rp, ci, srcs):
     return out
 
 
-def test_noalloc_matches_bfs_run_two_calls_in_a_row():
+def test_noalloc_matches_oracle_and_bfs_run_two_calls_in_a_row():
     import torch
     stream = torch.cuda.current_stream().cuda_stream
-    graphs = [graphgen.rmat(14, 16, seed=7), graphgen.grid(97, 131, 0.02, seed=9), graphgen.rmat(16, 16, seed=1)]
-    for rp, ci in graphs:
+    cases = [(graphgen.rmat(14, 16, seed=7), None), (graphgen.grid(97, 131, 0.02, seed=9), None),
+             (graphgen.rmat(16, 16, seed=1), None),
+             (graphgen.from_edges(5, []), [0, 4]),                                # nnz = 0
+             (graphgen.from_edges(7, [(i, i + 1) for i in range(6)]), [0, 3]),    # nnz = 12
+             (graphgen.from_edges(4, [(0, 1), (1, 2), (2, 3)]), [0, 2]),          # nnz = 6, not a multiple of 4
+             (graphgen.from_edges(4, [(1, 2), (2, 3), (1, 3)]), [0, 2])]          # vertex 0 isolated
+    for (rp, ci), srcs in cases:
         n, nnz = len(rp) - 1, len(ci)
-        srcs = graphgen.sample_sources(rp, 2, seed=5)
-        want = _reference(rp, ci, srcs)
+        srcs = graphgen.sample_sources(rp, 2, seed=5) if srcs is None else np.array(srcs, np.int32)
+        want = [oracle.bfs(rp, ci, int(s))[0] for s in srcs]
+        for w, o in zip(want, _reference(rp, ci, srcs)):
+            assert np.array_equal(w, o), "bfs_run differs from the oracle"
         # odd-length, unaligned device views of the CSR: the entry point must not care
         big = torch.zeros(nnz + 3, dtype=torch.int32, device="cuda")
-        big[1:1 + nnz] = torch.from_numpy(ci).cuda()
+        if nnz:
+            big[1:1 + nnz] = torch.from_numpy(ci).cuda()
         drp = torch.from_numpy(rp).cuda()
         dci = big[1:1 + nnz]
         level = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -62,9 +71,10 @@ def test_noalloc_matches_bfs_run_two_calls_in_a_row():
         for call in range(2):                       # two calls in a row, same inputs
             for s, w in zip(srcs, want):
                 level.fill_(123)
+                parent.fill_(123)
                 B.bfs_run_csr_noalloc(n, nnz, drp, dci, int(s), level, parent, stream)
                 lv = level.cpu().numpy()
-                assert np.array_equal(lv, w), f"call {call}, src {s}: levels differ from bfs_run"
+                assert np.array_equal(lv, w), f"n={n} call {call}, src {s}: levels differ from the oracle"
                 oracle.check_bfs_tree(rp, ci, int(s), lv, parent.cpu().numpy(), keys=keys)
 
 
