@@ -364,6 +364,15 @@ def bind_gpu_local_cpus(torch, dev):
 def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas):
     """One step = one bfs_run_batch over all sources (groups of 64 share a
     bitmask traversal); compared with the same sources run one at a time."""
+    line = measure_batch(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def measure_batch(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas):
+    """The bitmask batch's line (rank 0; None elsewhere)."""
     n, nnz = len(rp) - 1, len(ci)
     k = len(srcs)
     stream = torch.cuda.current_stream()
@@ -427,10 +436,15 @@ def run_batch_mode(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "clocks": clk.summary(), "gpu_launches": int(args.steps * (k + 63) // 64 * 3),
                 "sequential_gteps": round(seq_gteps, 3), "batch_speedup": round(gteps / seq_gteps, 2),
                 "levels": levels, "pulled_edges": int(work)}
-        print(json.dumps(line), flush=True)
+    else:
+        line = None
     B.bfs_destroy(g)
-    if dist:
-        dist.destroy_process_group()
+    return line
+
+
+def torch_device_index():
+    import torch
+    return torch.cuda.current_device()
 
 
 def serving_pool():
@@ -487,10 +501,11 @@ def run_serve_mode(args, B, torch):
     capacity = 1.0 / service.mean()                       # queries per second, one at a time
     loads = [float(x) for x in str(args.serve_load).split(",")]
     base_gaps = rng.exponential(1.0, size=N)              # one Poisson stream, rescaled per load
-    for load in loads:
-        serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, capacity, load, base_gaps, t_gen)
+    lines = [serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, capacity, load, base_gaps,
+                           t_gen) for load in loads]
     for h in handles:
         B.bfs_destroy(h)
+    return lines
 
 
 def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, capacity, load, base_gaps, t_gen):
@@ -532,15 +547,16 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
             B.bfs_server_submit(srv, int(gsel[i]), int(srcs[i]), None, None, i)
 
     th = threading.Thread(target=client, daemon=True)
-    th.start()
-    while len(done) < N:
-        for c in B.bfs_server_poll(srv, 256):
-            done[c.tag] = c
-        q, r = B.bfs_server_pending(srv)
-        if q == 0 and r == 0 and len(done) < N:
-            time.sleep(20e-6)
-    th.join()
-    makespan = time.perf_counter() - t0
+    with ClockSampler(torch_device_index()) as clk:
+        th.start()
+        while len(done) < N:
+            for c in B.bfs_server_poll(srv, 256):
+                done[c.tag] = c
+            q, r = B.bfs_server_pending(srv)
+            if q == 0 and r == 0 and len(done) < N:
+                time.sleep(20e-6)
+        th.join()
+        makespan = time.perf_counter() - t0
     B.bfs_server_destroy(srv)
     # the library stamps completions with the host's monotonic clock, the
     # clock time.perf_counter() reads on Linux: latency = done - arrival
@@ -565,9 +581,9 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
                                    "p99_ms": float(np.percentile(lat_fcfs, 99) * 1e3),
                                    "capacity_qps": capacity},
             "throughput_qps": N / makespan,
-            "failed": int(status_bad), "pool_build_s": round(t_gen, 1),
+            "failed": int(status_bad), "pool_build_s": round(t_gen, 1), "clocks": clk.summary(),
             "median_submit_delay_ms": clock_skew * 1e3}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -610,6 +626,9 @@ def main():
     ap.add_argument("--no-parents", action="store_true", help="levels only (batch mode)")
     ap.add_argument("--serve", action="store_true",
                     help="query server over the 32-graph pool: Poisson stream, p50/p99 latency")
+    ap.add_argument("--arms", default="batch,grid,serve",
+                    help="extra arms of the default R-MAT s22 line: batch (ER 2^20, 64-source bitmask), "
+                         "grid (4096^2 grid, default and autotuned), serve (32-graph pool); none = only the line")
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-load", default="0.7",
                     help="arrival rates as fractions of the one-at-a-time capacity, comma-separated; "
@@ -633,7 +652,8 @@ def main():
     from paper_2209_08764_gb300 import replicas
 
     if args.serve:
-        run_serve_mode(args, B, torch)
+        for ln in run_serve_mode(args, B, torch):
+            print(json.dumps(ln), flush=True)
         return
     ws, rank, local = dist_setup()
     dist = None
@@ -683,12 +703,92 @@ def main():
         if e_ws.get("j_per_traversal") and e_wi.get("j_per_traversal"):
             wi["energy_ratio_vs_work_sensitive"] = round(e_wi["j_per_traversal"] / e_ws["j_per_traversal"], 3)
         line["work_insensitive"] = wi
+    arms = [a for a in args.arms.split(",") if a and a != "none"]
+    if rank == 0 and args.workload == "rmat22" and not direction and not tuned and not args.per_phase:
+        # the rest of the metric on the same GPU, each arm on its own graph
+        # (rank 0 alone: the other ranks run none of them)
+        del rp, ci
+        if "batch" in arms:
+            line["er20_batch"] = arm_er20_batch(args, B, torch, dev, replicas, line)
+        if "grid" in arms:
+            line["grid4096"] = arm_grid4096(args, B, torch, dev, replicas)
+        if "serve" in arms:
+            line["serving"] = arm_serving(args, B, torch, line)
+        rp, ci = make_graph(w)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, rp, ci, srcs, args.cpu_budget)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def arm_er20_batch(args, B, torch, dev, replicas, line):
+    """Erdos-Renyi 2^20 (mean degree 16), 64 sources in one bitmask
+    traversal, against the same 64 sources one at a time through bfs_run on
+    the same graph."""
+    w = dict(WORKLOADS["er20"])
+    rp, ci = make_graph(w)
+    srcs = sources_for(w, rp, 0)
+    a = argparse.Namespace(**vars(args))
+    a.workload, a.no_parents = "er20", False
+    b = measure_batch(a, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas)
+    out = {k: b[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "clocks", "gpu_launches",
+                             "sequential_gteps", "batch_speedup", "levels", "pulled_edges")}
+    out["vs_rmat22_single_source_gteps"] = round(b["value"] / line["value"], 2)
+    return out
+
+
+GRID_TUNE_SPACE = {"cta_warps": [0, 16, 32], "small_level_edges": [0, 4096], "chunk_edges": [0, 32]}
+
+
+def arm_grid4096(args, B, torch, dev, replicas):
+    """4096^2 grid with 1% of edges deleted: the corner (deepest source) and 7
+    seeded sources, single-source S3BFS with the default options and with the
+    options the autotuner picks (coordinate descent over the CTA shape, the
+    small-level threshold and the grain, on the corner source).  Per level
+    also in SM cycles (us x the median sampled SM MHz), which takes the box's
+    clock out of the comparison."""
+    from paper_2209_08764_gb300 import autotune
+    w = dict(WORKLOADS["grid4096"])
+    rp, ci = make_graph(w)
+    srcs = sources_for(w, rp, 0)
+    a = argparse.Namespace(**vars(args))
+    a.workload, a.steps, a.no_energy, a.levels, a.dump = "grid4096", min(args.steps, 2), True, False, ""
+    out = {"config": config_of("grid4096", w, rp, ci)}
+    d = measure_single(a, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas, 0, summary=True)
+    t0 = time.perf_counter()
+    opts, key, info = autotune.tune(B, rp, ci, srcs[:1], symmetric=False, flags=B.BFS_VALIDATE, space=GRID_TUNE_SPACE,
+                                    reps=1)
+    tuned = autotune.resolve(opts, torch.cuda.get_device_properties(dev).multi_processor_count)
+    tune_s = time.perf_counter() - t0
+    t = measure_single(a, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas, 0, summary=True, tuned=tuned)
+    for name, r in (("default", d), ("autotuned", t)):
+        mhz = (r.get("clocks") or {}).get("sm_mhz")
+        out[name] = {k: r[k] for k in ("value", "unit", "ms_per_traversal_median", "ms_level_step_median",
+                                       "levels_median", "us_per_level_median", "roofline", "clocks", "gpu_launches",
+                                       "options")}
+        out[name]["kcycles_per_level_median"] = round(r["us_per_level_median"] * mhz / 1e3, 2) if mhz else None
+    out["autotune"] = {"class": key, "chosen": opts, "tuning_s": round(tune_s, 1), **info}
+    out["sources"] = "corner (vertex 0) + 7 seeded non-isolated vertices"
+    return out
+
+
+def arm_serving(args, B, torch, line):
+    """The 32-graph pool under a Poisson stream at 0.7 of the one-at-a-time
+    capacity and with every query at t = 0 (saturation), against the same
+    stream served first come, first served by single-source bfs_run."""
+    a = argparse.Namespace(**vars(args))
+    a.serve_load = "0.7,0"
+    lines = run_serve_mode(a, B, torch)
+    out = {"config": dict(lines[0]["config"], load=[0.7, "all at t=0"]), "queries": a.serve_queries}
+    for ln, name in zip(lines, ("load_0.7", "saturation")):
+        out[name] = {"gteps": ln["value"], "latency_ms": ln["latency_ms"], "throughput_qps": ln["throughput_qps"],
+                     "fcfs_one_at_a_time": ln["fcfs_one_at_a_time"], "failed": ln["failed"],
+                     "clocks": ln.get("clocks")}
+    out["pool_build_s"] = lines[0]["pool_build_s"]
+    out["vs_rmat22_single_source_gteps"] = round(lines[1]["value"] / line["value"], 3)
+    return out
 
 
 def level_bytes(n, rows):
@@ -839,6 +939,9 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "edges_scanned_per_traversal": float(recs[:, 3].mean()),
                 "gpu_launches": launches, "clocks": clk.summary(), "energy": energy,
                 "options": {f: getattr(opts, f) for f, _ in opts._fields_ if getattr(opts, f)},
+                "levels_median": float(np.median(recs[:, 5])),
+                "us_per_level_median": float(np.median(ms_loop * 1e3 / recs[:, 5])),
+                "ms_per_traversal_median": float(np.median(recs[:, 1])),
                 "create_s": round(t_create, 2)}
 
     # end to end through the C ABI: one bfs_run_batch call per step with

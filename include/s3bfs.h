@@ -32,6 +32,7 @@ extern "C" {
 #define BFS_E_NOMEM (-3)      /* device or pinned-host allocation failed, or bfs_opts.max_device_bytes reached */
 #define BFS_E_CUDA (-4)       /* a CUDA runtime call or kernel launch failed; see bfs_last_error() */
 #define BFS_E_TIMEOUT (-5)    /* a device-side wait (grid barrier or scan look-back) hit its limit */
+#define BFS_E_CHECK (-6)      /* checked build only: an index outside its array (the access was skipped) */
 
 /* ---- bfs_create_csr flags ---------------------------------------------- */
 #define BFS_DEVICE_PTRS 1 /* row_ptr / col_idx are device pointers (else host pointers) */
@@ -43,6 +44,9 @@ extern "C" {
 /* ---- bfs_opts.debug_flags (tests only) --------------------------------- */
 #define BFS_DEBUG_STALL_BARRIER 1 /* the last CTA never arrives at the first grid barrier,
                                      so the wait runs out and bfs_run returns BFS_E_TIMEOUT */
+#define BFS_DEBUG_CHECK_INJECT 2  /* checked build only: the source's row start is set past
+                                     col_idx, so the range check stops the traversal with
+                                     BFS_E_CHECK before any such access */
 
 /* Tuning knobs; a zero field takes the default.  NULL = all defaults. */
 typedef struct bfs_opts {
@@ -234,6 +238,19 @@ const char *bfs_last_error(void);
 /* bfs_graph_info -- n, nnz and the persistent grid (CTAs, warps) of a graph;
  * any output pointer may be NULL. */
 int bfs_graph_info(const bfs_graph *g, int32_t *n, int32_t *nnz, int32_t *ctas, int32_t *warps);
+
+/* bfs_run_frontiers -- debug form of bfs_run that also returns every level's
+ * frontier (Fig. 1: CurLevelVertices after the owner check and linearisation).
+ *
+ * Only the checked build (libs3bfs_checked.so, compiled with S3BFS_CHECKED=1:
+ * every global index range-checked, BFS_E_CHECK instead of an out-of-range
+ * access) implements it; the production library returns BFS_E_INVAL.
+ * frontiers_out: HOST array of n int32 receiving F_0, F_1, ... back to back
+ * in caller ids (F_0 = [src]); bfs_stats.per_level gives each n_l, and their
+ * sum is stats->reached.  Order within a level is arbitrary; as sets the
+ * levels are exact.  Other arguments as for bfs_run. */
+int bfs_run_frontiers(bfs_graph *g, int32_t src, int32_t *level_out, int32_t *parent_out, bfs_stats *stats,
+                      int32_t *frontiers_out);
 
 /* bfs_graph_device_bytes -- device memory the graph currently holds (what
  * bfs_opts.max_device_bytes caps), in bytes; -1 if g is NULL.  Buffers that

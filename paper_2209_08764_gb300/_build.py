@@ -1,9 +1,13 @@
-"""Build of the CUDA library ``libs3bfs.so`` (sm_103a) next to its sources.
+"""Build of the CUDA libraries (sm_103a) next to their sources.
 
-nvcc compiles the kernels + C ABI (``csrc/s3bfs.cu``) and the query server
-(``csrc/serve.cu``), g++ the host CSR helpers (``csrc/csr_host.cpp``), all in
-parallel; then nvcc links a shared library with the CUDA runtime linked
-statically.  Objects go to ``_build/`` (ignored).
+``libs3bfs.so`` is the product.  ``libs3bfs_checked.so`` is the same code
+compiled with ``S3BFS_CHECKED=1``: every global index of the level step is
+range-checked (an out-of-range one stops the traversal with BFS_E_CHECK
+instead of an access), and ``bfs_run_frontiers`` dumps every level's
+frontier.  nvcc compiles the kernels + C ABI (``csrc/s3bfs.cu``) and the
+query server (``csrc/serve.cu``) of both, g++ the host CSR helpers
+(``csrc/csr_host.cpp``), all in parallel; then nvcc links each shared library
+with the CUDA runtime linked statically.  Objects go to ``_build/`` (ignored).
 """
 from __future__ import annotations
 
@@ -18,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libs3bfs.so")
+LIB_CHECKED = os.path.join(HERE, "libs3bfs_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = [os.path.join(CSRC, f) for f in ("s3bfs.cu", "level_loop.cuh", "s3bfs_device.cuh", "msbfs.cuh", "host_internal.h", "serve.cu", "serve_device.cuh", "csr_host.cpp")] + \
     [os.path.join(INCLUDE, "s3bfs.h")]
@@ -32,10 +37,13 @@ def nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(s) > t for s in SOURCES)
+    for lib in (LIB, LIB_CHECKED):
+        if not os.path.exists(lib):
+            return True
+        t = os.path.getmtime(lib)
+        if any(os.path.getmtime(s) > t for s in SOURCES):
+            return True
+    return False
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -45,15 +53,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
         os.makedirs(BUILD, exist_ok=True)
         nv = nvcc()
-        obj_cu = os.path.join(BUILD, "s3bfs.o")
-        obj_serve = os.path.join(BUILD, "serve.o")
-        obj_cpp = os.path.join(BUILD, "csr_host.o")
         nvflags = [nv, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+        ptx = ["-Xptxas", "-v"] if verbose else []
+        obj = {k: os.path.join(BUILD, k + ".o") for k in ("s3bfs", "serve", "s3bfs_chk", "serve_chk", "csr_host")}
+        chk = ["-DS3BFS_CHECKED=1"]
         cmds = [
-            nvflags + ["-c", os.path.join(CSRC, "s3bfs.cu"), "-o", obj_cu] + (["-Xptxas", "-v"] if verbose else []),
-            nvflags + ["-c", os.path.join(CSRC, "serve.cu"), "-o", obj_serve] + (["-Xptxas", "-v"] if verbose else []),
+            nvflags + ["-c", os.path.join(CSRC, "s3bfs.cu"), "-o", obj["s3bfs"]] + ptx,
+            nvflags + ["-c", os.path.join(CSRC, "serve.cu"), "-o", obj["serve"]] + ptx,
+            nvflags + chk + ["-c", os.path.join(CSRC, "s3bfs.cu"), "-o", obj["s3bfs_chk"]],
+            nvflags + chk + ["-c", os.path.join(CSRC, "serve.cu"), "-o", obj["serve_chk"]],
             ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-c", os.path.join(CSRC, "csr_host.cpp"), "-o",
-             obj_cpp],
+             obj["csr_host"]],
         ]
         procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
         outs = [p.communicate()[0] for p in procs]
@@ -62,10 +72,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"build failed: {' '.join(c)}\n{o}")
             if verbose and o:
                 print(o)
-        tmp = LIB + f".tmp{os.getpid()}"
-        link = [nv, *ARCH, "-shared", "-o", tmp, obj_cu, obj_serve, obj_cpp]
-        r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")
-        os.replace(tmp, LIB)
+        for lib, objs in ((LIB, ("s3bfs", "serve", "csr_host")), (LIB_CHECKED, ("s3bfs_chk", "serve_chk", "csr_host"))):
+            tmp = lib + f".tmp{os.getpid()}"
+            link = [nv, *ARCH, "-shared", "-o", tmp] + [obj[k] for k in objs]
+            r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed: {' '.join(link)}\n{r.stdout}")
+            os.replace(tmp, lib)
         return LIB

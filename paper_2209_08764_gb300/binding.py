@@ -21,6 +21,7 @@ BFS_E_MULTIGRAPH = -2
 BFS_E_NOMEM = -3
 BFS_E_CUDA = -4
 BFS_E_TIMEOUT = -5
+BFS_E_CHECK = -6
 
 BFS_DEVICE_PTRS = 1
 BFS_VALIDATE = 2
@@ -28,10 +29,11 @@ BFS_DEDUP = 4
 BFS_SYMMETRIC = 8
 
 BFS_DEBUG_STALL_BARRIER = 1
+BFS_DEBUG_CHECK_INJECT = 2
 BFS_LEVEL_FIELDS = 9
 
 EXPORTS = ("bfs_create_csr", "bfs_run", "bfs_run_batch", "bfs_destroy", "bfs_strerror", "bfs_last_error",
-           "bfs_graph_info", "bfs_graph_device_bytes", "bfs_run_csr_noalloc", "bfs_server_create", "bfs_server_submit", "bfs_server_poll",
+           "bfs_graph_info", "bfs_graph_device_bytes", "bfs_run_frontiers", "bfs_run_csr_noalloc", "bfs_server_create", "bfs_server_submit", "bfs_server_poll",
            "bfs_server_pending", "bfs_server_destroy")
 
 
@@ -109,15 +111,17 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: libs3bfs.so, or the range-checked debug
+    build libs3bfs_checked.so when the environment sets S3BFS_LIBRARY=checked."""
+    return _build.LIB_CHECKED if os.environ.get("S3BFS_LIBRARY", "") == "checked" else _build.LIB
 
 
 def load():
-    """Load libs3bfs.so; raises if it has not been built."""
+    """Load the library (see library_path); raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
     lib = ctypes.CDLL(path)
@@ -140,6 +144,8 @@ def load():
                                    ctypes.POINTER(i32)]
     lib.bfs_graph_device_bytes.restype = ctypes.c_int64
     lib.bfs_graph_device_bytes.argtypes = [vp]
+    lib.bfs_run_frontiers.restype = ctypes.c_int
+    lib.bfs_run_frontiers.argtypes = [vp, i32, i32p, i32p, ctypes.POINTER(bfs_stats), i32p]
     lib.bfs_run_csr_noalloc.restype = ctypes.c_int
     lib.bfs_run_csr_noalloc.argtypes = [i32, i32, i32p, i32p, i32, i32p, i32p, vp]
     lib.bfs_server_create.restype = ctypes.c_int
@@ -219,6 +225,13 @@ def bfs_strerror(code: int) -> str:
 
 def bfs_last_error() -> str:
     return load().bfs_last_error().decode()
+
+
+def bfs_run_frontiers(g: int, src: int, level_out, parent_out, stats, frontiers_out) -> None:
+    rc = load().bfs_run_frontiers(g, int(src), _addr(level_out, "level_out"), _addr(parent_out, "parent_out"),
+                                  ctypes.byref(stats) if stats is not None else None,
+                                  _addr(frontiers_out, "frontiers_out"))
+    _check(rc)
 
 
 def bfs_graph_device_bytes(g: int) -> int:

@@ -61,6 +61,8 @@ struct bfs_graph {
   size_t dev_bytes = 0;  // device memory allocated through dalloc
   size_t dev_cap = 0;    // bfs_opts.max_device_bytes (0 = no cap)
   bool ms_arrive_grown = false;  // bitmask batches widened the barrier's arrival words
+  int32_t* d_fdump = nullptr;    // checked build: frontiers of one traversal in level order
+  bool fdump_on = false;
   // multi-source (bitmask) batches, allocated at the first batch
   bool symmetric = false;
   int batch_bitmask = 0;

@@ -81,6 +81,7 @@ extern "C" const char* bfs_strerror(int code) {
     case BFS_E_NOMEM: return "out of memory";
     case BFS_E_CUDA: return "CUDA error";
     case BFS_E_TIMEOUT: return "device wait timed out";
+    case BFS_E_CHECK: return "index out of range (checked build)";
     default: return "unknown error";
   }
 }
@@ -420,6 +421,9 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.beta = g->beta;
   p.gamma = g->gamma;
   p.n_live = g->n_live;
+#if S3BFS_CHECKED
+  p.fdump = g->fdump_on ? g->d_fdump : nullptr;
+#endif
   return p;
 }
 
@@ -510,6 +514,7 @@ static int traversal_error(const DevState& st, int32_t src) {
   if (st.err == BFS_E_TIMEOUT) return fail(BFS_E_TIMEOUT, "device wait %d ran out (src %d)", st.err_where, src);
   if (st.err == BFS_E_MULTIGRAPH)
     return fail(BFS_E_MULTIGRAPH, "next frontier larger than n: the graph repeats a neighbour (src %d)", src);
+  if (st.err == BFS_E_CHECK) return fail(BFS_E_CHECK, "range check %d failed (src %d)", st.err_where, src);
   return fail(st.err, "device error %d at %d (src %d)", st.err, st.err_where, src);
 }
 
@@ -611,6 +616,45 @@ extern "C" int bfs_run(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* p
   const int rc = run_one(g, src, level_out, parent_out, stats);
   if (cur != g->device) cudaSetDevice(cur);
   return rc;
+}
+
+extern "C" int bfs_run_frontiers(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* parent_out,
+                                 bfs_stats* stats, int32_t* frontiers_out) {
+#if !S3BFS_CHECKED
+  (void)g;
+  (void)src;
+  (void)level_out;
+  (void)parent_out;
+  (void)stats;
+  (void)frontiers_out;
+  return fail(BFS_E_INVAL, "the frontier dump is part of the checked build (libs3bfs_checked.so)");
+#else
+  if (!g) return fail(BFS_E_INVAL, "graph is NULL");
+  if (!level_out || !frontiers_out) return fail(BFS_E_INVAL, "level_out / frontiers_out is NULL");
+  if (src < 0 || src >= g->n) return fail(BFS_E_INVAL, "src %d out of range [0, %d)", src, g->n);
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != g->device) CUDA_TRY(cudaSetDevice(g->device));
+  int rc = BFS_OK;
+  if (!g->d_fdump) rc = dalloc(g, &g->d_fdump, (size_t)g->n + 4);
+  if (rc == BFS_OK) {
+    g->fdump_on = true;
+    rc = run_one(g, src, level_out, parent_out, stats);
+    g->fdump_on = false;
+  }
+  if (rc == BFS_OK) {
+    const size_t r = (size_t)std::min<long long>(g->h_st->reached, g->n);
+    CUDA_TRY(cudaMemcpy(frontiers_out, g->d_fdump, sizeof(int32_t) * r, cudaMemcpyDeviceToHost));
+    if (g->relabel) {
+      std::vector<int32_t> perm((size_t)g->n);
+      CUDA_TRY(cudaMemcpy(perm.data(), g->d_perm, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < r; ++i)
+        frontiers_out[i] = (unsigned)frontiers_out[i] < (unsigned)g->n ? perm[(size_t)frontiers_out[i]] : -1;
+    }
+  }
+  if (cur != g->device) cudaSetDevice(cur);
+  return rc;
+#endif
 }
 
 // ---- multi-source batches (bitmask frontiers) -----------------------------

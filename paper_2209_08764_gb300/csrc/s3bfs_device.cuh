@@ -152,6 +152,11 @@ struct Params {
   int32_t direction;  // 0: every level top-down; 1: direction-optimising
   int32_t alpha, beta, gamma;
   int32_t n_live;     // vertices of degree > 0 (the ones a bottom-up level can find)
+#if S3BFS_CHECKED
+  // checked build: every frontier in level order (F_0, F_1, ...), n entries
+  // (null: no dump)
+  int32_t* fdump;
+#endif
 };
 
 // ---------------------------------------------------------------------------
@@ -260,10 +265,34 @@ __device__ __forceinline__ int sm_id() {
   return s;
 }
 
+// Raise an error (the first one raised stays: a later error is a consequence).
 template <class P>
 __device__ __forceinline__ void set_err(const P& p, int code, int where) {
+  if (ld_relaxed(&p.st->err) != 0) return;
   st_relaxed(&p.st->err_where, where);
   st_relaxed(&p.st->err, code);
+}
+
+// Checked build (S3BFS_CHECKED=1, a debug library of its own): an index
+// outside its array sets BFS_E_CHECK with the check's id in err_where and
+// the access is skipped, so nothing faults; every CTA then leaves at its
+// next barrier.  The production build compiles every check away.
+#ifndef S3BFS_CHECKED
+#define S3BFS_CHECKED 0
+#endif
+template <class P>
+__device__ __forceinline__ bool in_range(const P& p, long long i, long long cap, int where) {
+#if S3BFS_CHECKED
+  if (i >= 0 && i < cap) return true;
+  set_err(p, BFS_E_CHECK, where);
+  return false;
+#else
+  (void)p;
+  (void)i;
+  (void)cap;
+  (void)where;
+  return true;
+#endif
 }
 
 __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
@@ -435,7 +464,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
   while (hi - lo > 1) {
     const int step = (hi - lo + kWarp - 1) / kWarp;
     const int idx = lo + lane * step;
-    const bool le = idx < hi && ld_cg(EX + idx) <= e_begin;
+    const bool le = idx < hi && in_range(p, idx, n_l + 1, 10) && ld_cg(EX + idx) <= e_begin;
     const unsigned m = __ballot_sync(kFull, le);
     const int J = 31 - __clz(m);
     lo += J * step;
@@ -449,7 +478,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
     // Stage a window of 32 frontier entries, one per lane: its first edge
     // EX[idx], the edge after its last EX[idx+1], its row start and vertex.
     const int idx = i + lane;
-    const bool in = idx < n_l;
+    const bool in = idx < n_l && in_range(p, n_l, (long long)p.n + 1, 11) && in_range(p, idx, p.n, 12);
     const int ex_lo = in ? ld_cg(EX + idx) : e_l;
     int ex_hi = __shfl_down_sync(kFull, ex_lo, 1);
     if (lane == kWarp - 1) ex_hi = in ? ld_cg(EX + idx + 1) : e_l;
@@ -486,7 +515,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
 #pragma unroll
       for (int r = 0; r < S3BFS_QPL; ++r) {
         const int q = base + r * kWarp + lane;
-        const bool act = q < Q;
+        bool act = q < Q;
 #if S3BFS_OWNER_REDUX
         // owner rank of quad q: the entries ending at or before the block
         // start B, plus those ending inside (B, q] (one bit each: quad ranges
@@ -498,6 +527,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
         const int w = min(wB + __popc(ends & lane_lt), kWarp - 1);
         const int4 R = rec[w];  // (a lane past Q may read a record this launch never wrote)
         const int qa = R.x + q;
+        act = act && in_range(p, qa, ((long long)p.nnz + 7) >> 2, 13);
         wp0[r] = R.y;
         wp1[r] = act ? R.z : 0;  // no valid position on a lane past Q
         wu[r] = R.w;
@@ -514,6 +544,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
         wp1[r] = __shfl_sync(kFull, p1, w);
         wu[r] = __shfl_sync(kFull, u, w);
         const int qa = wq0 + (q - wqoff);
+        act = act && in_range(p, qa, ((long long)p.nnz + 7) >> 2, 13);
 #endif
         c[r] = make_int4(0, 0, 0, 0);
         if (act) c[r] = ld_col4(col4 + qa, pol);
@@ -527,7 +558,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const bool known = cc[j] < hub_lim && ((s_hub[cc[j] >> 5] >> (cc[j] & 31)) & 1u);
-          vv[r][j] = pos[r] + j >= wp0[r] && pos[r] + j < wp1[r] && !known;
+          vv[r][j] = pos[r] + j >= wp0[r] && pos[r] + j < wp1[r] && !known && in_range(p, cc[j], p.n, 14);
           lv[r][j] = vv[r][j] ? ld_level(level + cc[j]) : 0;
         }
       }
@@ -542,6 +573,11 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
             st_relaxed(parent + cc[j], wu[r]);
           }
           cnt = emit(out, cnt, k, cc[j], wu[r], lane);
+#if S3BFS_CHECKED
+          // a chunk emits at most one candidate per edge of its region (the
+          // buffer's 32 spare pairs absorb the slot that would pass it)
+          if (!in_range(p, cnt, e_end - e_begin + 1, 15)) return e_end - e_begin;
+#endif
         }
       }
     }
@@ -613,6 +649,10 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
   int* RSn = np ? p.RS[1] : p.RS[0];
   int* EXn = np ? p.EX[1] : p.EX[0];
   const unsigned lt = (1u << lane) - 1u;
+#if S3BFS_CHECKED
+  // vertices of levels <= l (read before the publishing thread rewrites s_next)
+  const int vbase = p.fdump ? (s_next ? s_next->vcum : ld_relaxed(&p.st->ctrl[par].vcum)) : 0;
+#endif
 
   // ---- pass 1
   int K = 0, D = 0, K_stash = 0;
@@ -630,7 +670,7 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
     }
 #pragma unroll
     for (int r = 0; r < kCompactR; ++r)
-      pv[r] = pr[r].y != -2 ? ld_relaxed_nb(p.parent + pr[r].x) : -3;
+      pv[r] = pr[r].y != -2 && in_range(p, pr[r].x, p.n, 20) ? ld_relaxed_nb(p.parent + pr[r].x) : -3;
 #pragma unroll
     for (int r = 0; r < kCompactR; ++r) {
       keep[r] = pv[r] == pr[r].y;
@@ -684,7 +724,7 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
     st_release64(&S[b].word, (kFlagAgg << 62) | ep | (unsigned)Kc);
   }
   int kk = 0, dd = 0, cc = 0, ww = 0;
-  bool ok = true;
+  bool ok = in_range(p, b, p.max_chunks, 21);
   const long long t0 = global_ns();
   for (int j = threadIdx.x; j < b && ok; j += blockDim.x) {
     int it = 0;
@@ -775,6 +815,20 @@ __device__ S3BFS_COMPACT_QUAL bool compact_cta(const Params& p, int l, int par, 
       EXn[pos] = Dx + dpre[r];
     }
   }
+#if S3BFS_CHECKED
+  if (p.fdump) {
+    // the next frontier in level order: after the vertices of levels <= l
+    for (int base = 0; base < K_stash; base += kWarp * kCompactR)
+#pragma unroll
+      for (int r = 0; r < kCompactR; ++r) {
+        const int i = base + r * kWarp + lane;
+        if (i < K_stash && in_range(p, (long long)vbase + Kx + i, p.n, 22)) p.fdump[vbase + Kx + i] = ld_cg2(cand + i).x;
+      }
+#pragma unroll
+    for (int r = 0; r < kCompactR; ++r)
+      if (keep[r] && in_range(p, (long long)vbase + Kx + idx[r], p.n, 23)) p.fdump[vbase + Kx + idx[r]] = v[r];
+  }
+#endif
   if (b == (P_l - 1) / W && threadIdx.x == 0) {
     long long n_next = sPre[0], e_next = sPre[1], c_l = sPre[2], w_l = sPre[3];
 #pragma unroll
@@ -880,6 +934,7 @@ __device__ __forceinline__ unsigned ld_bits(const uint32_t* p) {
 #define S3BFS_BU_BITMAP 0
 #endif
 __device__ __forceinline__ bool in_frontier(const Params& p, const uint32_t* fb, int l, int u) {
+  if (!in_range(p, u, p.n, 32)) return false;
 #if S3BFS_BU_BITMAP
   (void)p;
   (void)l;
@@ -1023,6 +1078,7 @@ __device__ inline int bu_unvisited(const Params& p, int l, const uint32_t* fb, i
       const int v = (q << 7) + (j << 5) + lane;
       unv[j] = v < p.n && lv[j] < 0 && re[j] > rs[j];
       c0[j] = unv[j] ? __ldg(p.col_idx + rs[j]) : -1;
+      if (c0[j] >= 0 && !in_range(p, c0[j], p.n, 30)) c0[j] = -1;
     }
     bool hit[4];
 #pragma unroll
@@ -1070,6 +1126,7 @@ __device__ inline int bu_scan(const Params& p, int l, const uint32_t* fb, int gw
       const int i = b + s * kWarp + lane;
       act[s] = i < total;
       v[s] = act[s] ? ld_relaxed_nb(ulist + i) : 0;
+      if (act[s] && !in_range(p, v[s], p.n, 31)) act[s] = false;
     }
 #pragma unroll
     for (int s = 0; s < kBuV; ++s) {
@@ -1165,8 +1222,14 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
   for (long long i = tid; i < (p.hub_n >> 5); i += stride) p.hub_bits[i] = 0u;
   if (tid == 0) {
     const int rs = p.row_ptr[s], deg = p.row_ptr[s + 1] - rs;
+#if S3BFS_CHECKED
+    if (p.fdump) p.fdump[0] = s;
+#endif
     p.F[0][0] = s;
     p.RS[0][0] = rs;
+#if S3BFS_CHECKED
+    if (p.debug_flags & BFS_DEBUG_CHECK_INJECT) p.RS[0][0] = p.nnz + 8;  // caught by range check 13
+#endif
     p.EX[0][0] = 0;
     p.EX[0][1] = deg;
     DevState* st = p.st;

@@ -36,6 +36,22 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(B.EXPORTS) >= declared
 
 
+def test_checked_build_exports_the_same_symbols():
+    from paper_2209_08764_gb300 import _build
+    pkg.build()
+    chk = ctypes.CDLL(_build.LIB_CHECKED)
+    for name in sorted(_declared()):
+        assert hasattr(chk, name), f"{name} missing from the checked build"
+    chk.bfs_strerror.restype = ctypes.c_char_p
+    assert b"checked build" in chk.bfs_strerror(B.BFS_E_CHECK)
+
+
+def test_frontier_dump_needs_the_checked_build(lib):
+    # the production library refuses before touching the (NULL) graph
+    assert lib.bfs_run_frontiers(None, 0, None, None, None, None) == B.BFS_E_INVAL
+    assert "checked build" in B.bfs_last_error()
+
+
 def test_host_only_calls(lib):
     assert B.bfs_strerror(0) == "ok"
     assert "timed out" in B.bfs_strerror(B.BFS_E_TIMEOUT)
