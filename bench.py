@@ -208,24 +208,60 @@ class EnergyMeter:
         return e.value if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.h, ctypes.byref(e)) == 0 else None
 
 
-def energy_per_traversal(meter, run_one, srcs, seconds=1.5):
-    """Joules per traversal and mean power over >= seconds of back-to-back
-    traversals of the sources (NVML energy counter around the loop)."""
+def energy_per_traversal(meter, run_one, srcs, seconds=0.6, repeats=3):
+    """Joules per traversal and mean power: NVML's energy counter around
+    >= seconds of back-to-back traversals of the sources, repeated; the mean
+    and the standard deviation over the repeats."""
     import torch
     if meter is None or meter.read_mj() is None:
         return None
-    torch.cuda.synchronize()
-    e0, t0, k = meter.read_mj(), time.perf_counter(), 0
-    while time.perf_counter() - t0 < seconds:
-        for s in srcs:
-            run_one(int(s))
-            k += 1
-    torch.cuda.synchronize()
-    e1, t1 = meter.read_mj(), time.perf_counter()
-    if e1 is None or e1 <= e0:
+    j, w, ks = [], [], []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        e0, t0, k = meter.read_mj(), time.perf_counter(), 0
+        while time.perf_counter() - t0 < seconds:
+            for s in srcs:
+                run_one(int(s))
+                k += 1
+        torch.cuda.synchronize()
+        e1, t1 = meter.read_mj(), time.perf_counter()
+        if e1 is None or e1 <= e0:
+            return None
+        j.append((e1 - e0) * 1e-3 / k)
+        w.append((e1 - e0) * 1e-3 / (t1 - t0))
+        ks.append(k)
+    return {"j_per_traversal": float(np.mean(j)), "j_per_traversal_std": float(np.std(j, ddof=1)),
+            "avg_w": float(np.mean(w)), "repeats": repeats, "traversals": int(sum(ks)),
+            "seconds_per_repeat": seconds, "source": "NVML total energy counter"}
+
+
+def sms_total(torch, dev):
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def active_sms_summary(rows, sms):
+    """Active SMs per level of one traversal (the first source's per-level
+    records: SMs hosting at least one warp with a chunk); the rest of the SMs
+    are parked at the grid barrier for that level."""
+    a = np.asarray(rows)[:, 4].astype(np.int64) if rows is not None and len(rows) else np.zeros(0, np.int64)
+    if len(a) == 0:
         return None
-    return {"j_per_traversal": (e1 - e0) * 1e-3 / k, "avg_w": (e1 - e0) * 1e-3 / (t1 - t0),
-            "traversals": k, "seconds": round(t1 - t0, 2), "source": "NVML total energy counter"}
+    out = {"sms": int(sms), "mean": round(float(a.mean()), 2), "levels_on_one_sm": int((a <= 1).sum()),
+           "levels": int(len(a))}
+    if len(a) <= 64:
+        out["per_level"] = a.tolist()
+    return out
+
+
+def ratio_with_error(a, b):
+    """a / b of two energy records, with the standard deviation propagated from
+    the repeats of each (first order)."""
+    if not a or not b or not a.get("j_per_traversal") or not b.get("j_per_traversal"):
+        return None
+    r = a["j_per_traversal"] / b["j_per_traversal"]
+    ra = a.get("j_per_traversal_std", 0.0) / a["j_per_traversal"]
+    rb = b.get("j_per_traversal_std", 0.0) / b["j_per_traversal"]
+    return {"ratio": round(r, 4), "std": round(r * (ra * ra + rb * rb) ** 0.5, 4)}
 
 
 def dist_setup():
@@ -390,20 +426,31 @@ def measure_batch(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas
     edges_per_step = sum(teps)
     levels = max(st[i].num_levels for i in range(k))
     work = st[0].work_edges
+    # enough steps for the clock sampler (100 ms period) to see the timed region
+    torch.cuda.synchronize()
+    t_one = time.perf_counter()
+    B.bfs_run_batch(g, S, k, L, P, None)
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t_one
+    steps = max(args.steps, int(np.ceil(0.4 / max(t_one, 1e-6))))
     if dist:
+        # every rank times the same number of steps
+        t = torch.tensor([steps], device=torch.device("cuda", dev))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        steps = int(t.item())
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms_kernel = []
     with ClockSampler(dev) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             B.bfs_run_batch(g, S, k, L, P, st)
             ms_kernel.append(st[0].ms_level_step)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    ms_max, total_edges = replicas.aggregate(dist, ms, edges_per_step * args.steps,
+    ms_max, total_edges = replicas.aggregate(dist, ms, edges_per_step * steps,
                                              torch.device("cuda", dev) if dist else None)
     gteps = total_edges / (ms_max / 1e3) / 1e9
     # the same sources one at a time through bfs_run (single-source S3BFS)
@@ -421,19 +468,24 @@ def measure_batch(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas
     seq_gteps = edges_per_step / (e0.elapsed_time(e1) / 1e3) / 1e9
     peak, peak_kind = peaks()
     kms = float(np.mean(ms_kernel))
-    bytes_launch = 12.0 * work + 24.0 * n * levels
+    # pull: 12 B per pulled edge (col_idx + the neighbour's frontier mask) and
+    # 24 B per vertex per level (seen read + write, next frontier mask); the
+    # k x n levels (and parents) written once
+    k_out = 8 if P is not None else 4
+    bytes_launch = 12.0 * work + 24.0 * n * levels + k_out * k * n
     achieved = bytes_launch / (kms / 1e3) / 1e9
     if rank == 0:
-        line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        line = {"metric": METRIC, "value": round(gteps, 3), "unit": "GTEPS", "n_gpus": ws, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": dict(config_of(args.workload, w, rp, ci), mode="batch-bitmask", k=k,
                                parents=not args.no_parents),
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
                              "kernel": "k_msbfs", "algorithmic_bytes_per_launch": bytes_launch,
-                             "avg_launch_ms": kms, "model": "12 B per pulled edge + 24 B per vertex per level"},
-                "clocks": clk.summary(), "gpu_launches": int(args.steps * (k + 63) // 64 * 3),
+                             "avg_launch_ms": kms, "model": "12 B per pulled edge + 24 B per vertex per level + 4 B (8 with parents) "
+                                      "per (source, vertex) output"},
+                "clocks": clk.summary(), "gpu_launches": int(steps * st[0].launches * ((k + 63) // 64)),
                 "sequential_gteps": round(seq_gteps, 3), "batch_speedup": round(gteps / seq_gteps, 2),
                 "levels": levels, "pulled_edges": int(work)}
     else:
@@ -699,9 +751,7 @@ def main():
         wi = measure_single(args, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas, 0, summary=True,
                             tuned=dict(tuned or {}, work_insensitive=1))
         wi["time_ratio_vs_work_sensitive"] = round(wi["ms_level_step_median"] / line["ms_level_step_median"], 3)
-        e_ws, e_wi = (line.get("energy") or {}), (wi.get("energy") or {})
-        if e_ws.get("j_per_traversal") and e_wi.get("j_per_traversal"):
-            wi["energy_ratio_vs_work_sensitive"] = round(e_wi["j_per_traversal"] / e_ws["j_per_traversal"], 3)
+        wi["energy_ratio_vs_work_sensitive"] = ratio_with_error(wi.get("energy"), line.get("energy"))
         line["work_insensitive"] = wi
     arms = [a for a in args.arms.split(",") if a and a != "none"]
     if rank == 0 and args.workload == "rmat22" and not direction and not tuned and not args.per_phase:
@@ -733,13 +783,13 @@ def arm_er20_batch(args, B, torch, dev, replicas, line):
     a = argparse.Namespace(**vars(args))
     a.workload, a.no_parents = "er20", False
     b = measure_batch(a, w, rp, ci, srcs, B, torch, None, 1, 0, dev, replicas)
-    out = {k: b[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "clocks", "gpu_launches",
+    out = {k: b[k] for k in ("value", "unit", "steps", "ms_per_step", "config", "roofline", "clocks", "gpu_launches",
                              "sequential_gteps", "batch_speedup", "levels", "pulled_edges")}
     out["vs_rmat22_single_source_gteps"] = round(b["value"] / line["value"], 2)
     return out
 
 
-GRID_TUNE_SPACE = {"cta_warps": [0, 16, 32], "small_level_edges": [0, 4096], "chunk_edges": [0, 32]}
+GRID_TUNE_SPACE = {"cta_warps": [0, 8, 32], "small_level_edges": [0, 8192], "chunk_edges": [0, 32]}
 
 
 def arm_grid4096(args, B, torch, dev, replicas):
@@ -771,7 +821,43 @@ def arm_grid4096(args, B, torch, dev, replicas):
         out[name]["kcycles_per_level_median"] = round(r["us_per_level_median"] * mhz / 1e3, 2) if mhz else None
     out["autotune"] = {"class": key, "chosen": opts, "tuning_s": round(tune_s, 1), **info}
     out["sources"] = "corner (vertex 0) + 7 seeded non-isolated vertices"
+    if not args.no_energy:
+        # the paper's comparison where it matters most: thousands of small
+        # levels, each on the warps (and SMs) it needs, or on every warp
+        ws = energy_run(B, torch, dev, rp, ci, srcs[:1], {})
+        wi = energy_run(B, torch, dev, rp, ci, srcs[:1], {"work_insensitive": 1})
+        out["work_sensitive_vs_insensitive"] = {
+            "source": "corner", "work_sensitive": ws, "work_insensitive": wi,
+            "time_ratio_insensitive_vs_sensitive": round(wi["ms_per_traversal"] / ws["ms_per_traversal"], 3),
+            "energy_ratio_insensitive_vs_sensitive": ratio_with_error(wi["energy"], ws["energy"])}
     return out
+
+
+def energy_run(B, torch, dev, rp, ci, srcs, opts):
+    """Time, active SMs per level and NVML energy of single-source traversals
+    with the given options."""
+    n = len(rp) - 1
+    stream = torch.cuda.current_stream()
+    o = B.bfs_opts()
+    for k, v in opts.items():
+        setattr(o, k, int(v))
+    g = B.bfs_create_csr(n, len(ci), rp, ci, 0, o, stream.cuda_stream)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    try:
+        cap = 1 << 16
+        buf = (ctypes.c_int32 * (cap * B.BFS_LEVEL_FIELDS))()
+        st = B.bfs_stats()
+        st.per_level = ctypes.cast(buf, ctypes.POINTER(ctypes.c_int32))
+        st.per_level_cap = cap
+        B.bfs_run(g, int(srcs[0]), level, None, None)
+        B.bfs_run(g, int(srcs[0]), level, None, st)
+        L = min(st.num_levels, cap)
+        rows = np.frombuffer(buf, dtype=np.int32)[:L * B.BFS_LEVEL_FIELDS].reshape(L, B.BFS_LEVEL_FIELDS)
+        energy = energy_per_traversal(EnergyMeter(torch, dev), lambda s: B.bfs_run(g, s, level, None, None), srcs)
+        return {"options": opts, "ms_per_traversal": float(st.ms_total), "levels": int(st.num_levels),
+                "active_sms": active_sms_summary(rows, sms_total(torch, dev)), "energy": energy}
+    finally:
+        B.bfs_destroy(g)
 
 
 def arm_serving(args, B, torch, line):
@@ -942,6 +1028,7 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "levels_median": float(np.median(recs[:, 5])),
                 "us_per_level_median": float(np.median(ms_loop * 1e3 / recs[:, 5])),
                 "ms_per_traversal_median": float(np.median(recs[:, 1])),
+                "active_sms": active_sms_summary(first_rows, sms_total(torch, dev)),
                 "create_s": round(t_create, 2)}
 
     # end to end through the C ABI: one bfs_run_batch call per step with
@@ -1005,7 +1092,8 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                 "ms_level_step_min": float(np.min(ms_loop)), "ms_level_step_max": float(np.max(ms_loop)),
                 "levels_median": float(np.median(recs[:, 5])),
                 "us_per_level_median": float(np.median(ms_loop * 1e3 / recs[:, 5])),
-                "ctas": info["ctas"], "warps": info["warps"]}
+                "ctas": info["ctas"], "warps": info["warps"],
+                "active_sms": active_sms_summary(first_rows, sms_total(torch, dev))}
         if e2e:
             line["e2e"] = e2e
         line["energy"] = energy

@@ -59,9 +59,9 @@ typedef struct bfs_opts {
   int32_t persistent;       /* 1 (default): one cooperative launch runs all levels,
                                separated by device grid barriers; -1: one launch per
                                phase with a host read of the level sizes in between */
-  int32_t work_insensitive; /* 1: every warp is active at every level (chunks of
-                               ceil(e_l / P) edges), the comparison arm of the
-                               Experimental Results */
+  int32_t work_insensitive; /* 1: every warp of the grid is active at every level
+                               (chunks of ceil(e_l / P) edges; no small-level mode),
+                               the comparison arm of the Experimental Results */
   int32_t spin_limit_ms;    /* limit of every device-side wait; default 1000 ms */
   int32_t debug_flags;      /* BFS_DEBUG_* (tests only); default 0 */
   int32_t relabel;          /* visited bits in shared memory: 0 (default) = for every
@@ -84,7 +84,7 @@ typedef struct bfs_opts {
   int32_t cta_warps;        /* warps per CTA of the level loop: 8 (four CTAs per SM),
                                or 16, 24, 32 (one CTA per SM, one copy of the
                                shared-memory visited bits; 128, 80 or 64 registers a
-                               thread); 0 = 32 when visited bits are kept, else 8 */
+                               thread); 0 = 32 when visited bits are kept, else 16 */
   int32_t direction;        /* 0 (default): every level top-down, the S3BFS level step.
                                1: direction-optimising (needs BFS_SYMMETRIC, else
                                bfs_create_csr fails with BFS_E_INVAL): a level whose

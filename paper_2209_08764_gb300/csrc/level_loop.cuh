@@ -57,8 +57,10 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
     work = e_end - e_begin;
     if (e_begin < e_end) cnt = explore_chunk<W>(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, s_hub, hub_lim);
   }
+  // a CTA without a chunk in this level waits with a longer back-off
+  const bool idle = (int)blockIdx.x * W >= P_l;
   if (GRID) {
-    if (!grid_sync(p, ++*bar)) return false;
+    if (!grid_sync(p, ++*bar, idle ? kSleepIdle : kSleepBusy)) return false;
   } else {
     __syncthreads();
   }
@@ -74,6 +76,7 @@ __device__ __forceinline__ bool one_level(const Params& p, int l, int n_l, int e
                    GRID ? nullptr : s_ctrl);
   }
   if (GRID) {
+    // (the next level may give every CTA work: no back-off here)
     if (!grid_sync(p, ++*bar)) return false;
   } else {
     __syncthreads();
@@ -159,6 +162,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 8 ? 4 : 1) k_level_loop(Params
   const int P = gridDim.x * W;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) p.cta_smid[blockIdx.x] = sm_id();
+  init_cta_err();
   __shared__ LevelCtrl s_ctrl;  // CTA 0 during a streak: the current level's control block
   int bar = 0, l = 0;
   long long acc[4] = {0, 0, 0, 0};  // reached, edges, candidates, work (leader)
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 8 ? 4 : 1) k_level_loop(Params
     }
     if (small && blockIdx.x != 0) {
       // parked at one grid barrier while CTA 0 runs the small levels
-      if (!grid_sync(p, ++bar)) break;
+      if (!grid_sync(p, ++bar, kSleepParked)) break;
       l = ld_relaxed(&p.st->resume_level);
       if (p.hub_n > 0) {
         build_hub_bits(p, gw, P);

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
   long long my_edges = 0;
   const int lane = threadIdx.x & (kWarp - 1);
   const int wib = threadIdx.x >> 5;
+  init_cta_err();
   uint8_t* s_off = ms_dyn + wib * 64 * kWarp;  // [source bit][lane]
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nthreads = (long long)gridDim.x * blockDim.x;

@@ -265,9 +265,23 @@ __device__ __forceinline__ int sm_id() {
   return s;
 }
 
+// Per-CTA flag in shared memory: this CTA raised an error.  Its next grid
+// barrier arrival carries it, so the barrier learns of the error without a
+// read of the global error word.  Every kernel that uses grid_sync clears it
+// at its start (init_cta_err).
+__device__ __forceinline__ int& cta_err_flag() {
+  __shared__ int f;
+  return f;
+}
+__device__ __forceinline__ void init_cta_err() {
+  if (threadIdx.x == 0) cta_err_flag() = 0;
+  __syncthreads();
+}
+
 // Raise an error (the first one raised stays: a later error is a consequence).
 template <class P>
 __device__ __forceinline__ void set_err(const P& p, int code, int where) {
+  cta_err_flag() = 1;
   if (ld_relaxed(&p.st->err) != 0) return;
   st_relaxed(&p.st->err_where, where);
   st_relaxed(&p.st->err, code);
@@ -330,32 +344,52 @@ __host__ __device__ inline void level_sizing(int e_l, int P, int grain, int work
 // CTAs return false.  Returns false, in every CTA, when any CTA raised an
 // error before the barrier.
 // ---------------------------------------------------------------------------
+// sleep_cap: the longest pause between two polls of the release word by a
+// waiting CTA (ns).  A CTA with work polls every 64 ns; a CTA with nothing
+// to do before the release backs off exponentially up to the cap: up to
+// 512 ns for a CTA without a chunk in a level (the phase after the release
+// takes several microseconds, so a late wake-up delays nobody), 2048 ns for
+// one parked while CTA 0 runs a streak of small levels.
+constexpr int kSleepBusy = 64;
+constexpr int kSleepIdle = 512;
+constexpr int kSleepParked = 2048;
+// flagged: the CTAs' error flags ride on their arrival words (every error
+// raised in the launch concerns p.st).  A launch whose CTAs also raise errors
+// that must not stop the grid (per-query errors of the query server) passes
+// false: CTA 0 then reads p.st->err once the arrivals are in.
 template <class P>
-__device__ bool grid_sync(const P& p, int epoch) {
+__device__ bool grid_sync(const P& p, int epoch, int sleep_cap = kSleepBusy, bool flagged = true) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     const bool stall =
         (p.debug_flags & BFS_DEBUG_STALL_BARRIER) && epoch == 1 && blockIdx.x == gridDim.x - 1;
     __threadfence();
-    if (!stall) st_relaxed(&p.bar_arrive[blockIdx.x], epoch);
+    // arrival word: 2 * epoch, + 1 if this CTA raised an error
+    if (!stall) st_relaxed(&p.bar_arrive[blockIdx.x], 2 * epoch + (flagged && cta_err_flag() ? 1 : 0));
   }
   const unsigned target = (unsigned)epoch;
   if (blockIdx.x == 0) {
     // CTA 0 gathers the arrivals, four words per 16-byte load (the arrival
-    // array is padded to a multiple of four entries)
-    bool ok = true;
+    // array is padded to a multiple of four entries); an arrival's low bit
+    // says that CTA raised an error before it arrived
+    bool ok = true, raised = false;
     const long long t0 = global_ns();
     const int groups = ((int)gridDim.x + 3) >> 2;
     const int4* arr4 = reinterpret_cast<const int4*>(p.bar_arrive);
+    const int e2 = 2 * epoch;
     for (int q = threadIdx.x; q < groups && ok; q += blockDim.x) {
       const int base = q << 2;
       int it = 0;
       while (true) {
         const int4 a = ld_relaxed4(arr4 + q);
-        const bool done = (a.x >= epoch || base + 0 >= (int)gridDim.x) && (a.y >= epoch || base + 1 >= (int)gridDim.x) &&
-                          (a.z >= epoch || base + 2 >= (int)gridDim.x) && (a.w >= epoch || base + 3 >= (int)gridDim.x);
-        if (done) break;
+        const bool done = (a.x >= e2 || base + 0 >= (int)gridDim.x) && (a.y >= e2 || base + 1 >= (int)gridDim.x) &&
+                          (a.z >= e2 || base + 2 >= (int)gridDim.x) && (a.w >= e2 || base + 3 >= (int)gridDim.x);
+        if (done) {
+          raised |= ((a.x & 1) && base + 0 < (int)gridDim.x) || ((a.y & 1) && base + 1 < (int)gridDim.x) ||
+                    ((a.z & 1) && base + 2 < (int)gridDim.x) || ((a.w & 1) && base + 3 < (int)gridDim.x);
+          break;
+        }
         ++it;
         if ((it & 31) == 0 && ld_relaxed(&p.st->err) != 0) {
           ok = false;
@@ -369,15 +403,15 @@ __device__ bool grid_sync(const P& p, int epoch) {
         if (it > 64) __nanosleep(64);
       }
     }
-    ok = __syncthreads_and(ok);
+    ok = __syncthreads_and(ok && !raised);
     if (threadIdx.x == 0) {
-      __threadfence();  // the arrivals seen above happen before the error check
-      const bool err = !ok || ld_relaxed(&p.st->err) != 0;
+      __threadfence();  // the arrivals seen above happen before the error check; the release after this CTA's writes
+      const bool err = !ok || (flagged ? cta_err_flag() != 0 : ld_relaxed(&p.st->err) != 0);
       st_relaxed(&p.st->bar_release, (int)(2u * target + (err ? 1u : 0u)));
       s_ok = !err;
     }
   } else if (threadIdx.x == 0) {
-    int ok = 1, it = 0;
+    int ok = 1, it = 0, nap = kSleepBusy;
     long long t0 = global_ns();
     int prog = ld_relaxed(&p.st->progress);
     while (true) {
@@ -405,7 +439,10 @@ __device__ bool grid_sync(const P& p, int epoch) {
         ok = 0;
         break;
       }
-      if (it > 64) __nanosleep(64);
+      if (it > 64) {
+        __nanosleep(nap);
+        nap = min(2 * nap, sleep_cap);
+      }
     }
     __threadfence();
     s_ok = ok;
@@ -431,6 +468,9 @@ __device__ __forceinline__ int emit(int2* out, int cnt, bool k, int v, int u, in
 // means the vertex already has a level, so its level[] test is skipped.
 #ifndef S3BFS_EXPLORE_QUAL
 #define S3BFS_EXPLORE_QUAL inline
+#endif
+#ifndef S3BFS_PPL
+#define S3BFS_PPL 1  // probes per lane in a round of the start-point search (1: 32-ary)
 #endif
 #ifndef S3BFS_OWNER_REDUX
 #define S3BFS_OWNER_REDUX 1  // 1: quad owners by ballot + OR-reduction and shared records; 0: shuffle search
@@ -462,11 +502,19 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
   // that is still <= e_begin.  Invariant: EX[lo] <= e_begin < EX[hi].
   int lo = 0, hi = n_l;
   while (hi - lo > 1) {
-    const int step = (hi - lo + kWarp - 1) / kWarp;
-    const int idx = lo + lane * step;
-    const bool le = idx < hi && in_range(p, idx, n_l + 1, 10) && ld_cg(EX + idx) <= e_begin;
-    const unsigned m = __ballot_sync(kFull, le);
-    const int J = 31 - __clz(m);
+    // S3BFS_PPL probes per lane a round (lane L probes PPL*L .. PPL*L + PPL - 1)
+    constexpr int kPpl = S3BFS_PPL;
+    constexpr int kProbes = kPpl * kWarp;
+    const int step = (hi - lo + kProbes - 1) / kProbes;
+    int cntle = 0;
+#pragma unroll
+    for (int t = 0; t < kPpl; ++t) {
+      const int idx = lo + (kPpl * lane + t) * step;
+      cntle += (idx < hi && in_range(p, idx, n_l + 1, 10) && ld_cg(EX + idx) <= e_begin) ? 1 : 0;
+    }
+    // probes are in increasing order and EX is non-decreasing, so the probes
+    // <= e_begin form a prefix: its length minus one is the last such probe
+    const int J = __reduce_add_sync(kFull, cntle) - 1;
     lo += J * step;
     hi = min(lo + step, hi);
   }

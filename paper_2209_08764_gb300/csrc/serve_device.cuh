@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
   __shared__ int3 s_lne[kMaxSlots];
   const int wib = threadIdx.x >> 5;
   const bool watch = blockIdx.x == 0 && threadIdx.x == 0 && sp.wake != nullptr;
+  init_cta_err();
   int bar = 0;
   for (int it = 0; it < sp.max_levels; ++it) {
     // read early: the host-memory load overlaps the step's work
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
           cnt = explore_chunk<W>(p, l, par, n_l, e_l, e_begin, e_end, p.cand + e_begin, nullptr, 0);
       }
     }
-    if (!grid_sync(sp, ++bar)) break;
+    if (!grid_sync(sp, ++bar, kSleepBusy, false)) break;
     if (sd) {
       const Params& p = sd->p;
       if (P_l == 0) {
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParam
       }
     }
     if (woke) st_relaxed(sp.finished, 1);  // a query waits: end after this step
-    if (!grid_sync(sp, ++bar)) break;
+    if (!grid_sync(sp, ++bar, kSleepBusy, false)) break;
     // a finished query or a waiting one ends the launch at the next step's
     // assignment (retire and admit before going on)
   }

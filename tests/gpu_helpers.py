@@ -39,6 +39,8 @@ class Dev:
         # levels with at most this many edges run on one CTA (small-level mode)
         wpc = self.info["warps"] // self.info["ctas"]
         self.small = 256 * wpc if self._small_opt == 0 else (0 if self._small_opt < 0 else self._small_opt)
+        if opts.get("work_insensitive"):
+            self.small = 0          # every level on the whole grid
         self.level = torch.empty(self.n, dtype=torch.int32, device="cuda")
         self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
 

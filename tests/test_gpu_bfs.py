@@ -130,9 +130,7 @@ def test_work_insensitive_uses_every_warp(rmat16):
     try:
         _, _, st, pl = d.run(int(srcs[0]), per_level_cap=64)
         P = d.info["warps"]
-        big = pl[:, 1] > d.small
-        assert np.all(pl[big, 3] == P)
-        assert np.all(pl[(pl[:, 1] > 0) & ~big, 3] == P // d.info["ctas"])
+        assert np.all(pl[pl[:, 1] > 0, 3] == P), "a level left warps idle"
     finally:
         d.close()
 
