@@ -623,7 +623,7 @@ def serve_at_load(args, B, stream, handles, graphs, gsel, srcs, service, teps, c
             "config": {"workload": "serving-pool32", "graphs": [g[0] for g in graphs], "queries": N,
                        "load": load if load > 0 else "all at t=0", "lambda_qps": lam if load > 0 else None,
                        "slots": args.serve_slots, "local_levels": args.serve_local_levels,
-                       "cta_warps": args.serve_cta_warps or 8,
+                       "cta_warps": args.serve_cta_warps or 16,
                        "levels_per_launch": args.serve_levels_per_launch or 64,
                        "arrivals": "Poisson, graph uniform over the pool, source uniform over non-isolated, seed 5"},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
@@ -688,7 +688,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-levels-per-launch", type=int, default=0,
                     help="bfs_server_opts.levels_per_launch (0 = the library default, 64)")
-    ap.add_argument("--serve-cta-warps", type=int, default=0, help="bfs_server_opts.cta_warps (0 = 8)")
+    ap.add_argument("--serve-cta-warps", type=int, default=0, help="bfs_server_opts.cta_warps (0 = 16)")
     ap.add_argument("--serve-local-levels", type=int, default=0,
                     help="bfs_server_opts.local_levels (0 = off)")
     args = ap.parse_args()

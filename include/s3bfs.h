@@ -307,7 +307,7 @@ typedef struct bfs_server_opts {
                                 query finishes, and after the current step when a
                                 submission arrives) */
   int32_t chunk_edges;       /* grain, as bfs_opts.chunk_edges; 0 = 64 */
-  int32_t cta_warps;         /* 8 or 32 warps per CTA; 0 = 8 */
+  int32_t cta_warps;         /* 8, 16 or 32 warps per CTA; 0 = 16 */
   int32_t spin_limit_ms;     /* device wait limit; 0 = 1000 */
   int32_t local_levels;      /* > 0: a query that gets one CTA and whose level has at most
                                 256 edges per warp runs up to this many levels per step on

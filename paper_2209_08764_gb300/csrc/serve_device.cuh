@@ -153,7 +153,7 @@ __device__ void serve_local(const ServeParams& sp, SlotDev* sd) {
 
 // One launch: up to sp.max_levels levels of every running query.
 template <int W>
-__global__ void __launch_bounds__(W * kWarp, W == 32 ? 1 : 4) k_serve(ServeParams sp) {
+__global__ void __launch_bounds__(W * kWarp, W == 8 ? 4 : 1) k_serve(ServeParams sp) {
   __shared__ int s_q, s_rank, s_size;
   __shared__ long long s_w[kMaxSlots];
   __shared__ int3 s_lne[kMaxSlots];

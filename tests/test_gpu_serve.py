@@ -58,7 +58,7 @@ def _drain(s, expect):
     return got
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(slots=2), dict(levels_per_launch=1), dict(cta_warps=32),
+@pytest.mark.parametrize("opts", [dict(), dict(slots=2), dict(levels_per_launch=1), dict(cta_warps=32), dict(cta_warps=8),
                                   dict(slots=5, levels_per_launch=3, chunk_edges=7), dict(local_levels=8),
                                   dict(local_levels=64), dict(local_levels=3, cta_warps=32, slots=3)],
                          ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()) or "default")
