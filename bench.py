@@ -77,34 +77,41 @@ def strip_c_comments(src: str) -> str:
     return " ".join(src.split())
 
 
-def kernel_source_hash():
-    """First 16 hex digits of the sha256 of the level loop's device sources
-    (its kernels and their building blocks, comments stripped): the key under
-    which a committed ncu summary is valid.  Host code is not part of it."""
+KERNEL_SOURCES = {
+    "level_loop": ("paper_2209_08764_gb300/csrc/level_loop.cuh", "paper_2209_08764_gb300/csrc/s3bfs_device.cuh"),
+    "msbfs": ("paper_2209_08764_gb300/csrc/msbfs.cuh", "paper_2209_08764_gb300/csrc/s3bfs_device.cuh"),
+}
+
+
+def kernel_source_hash(kernel="level_loop"):
+    """First 16 hex digits of the sha256 of a kernel's device sources (the
+    kernel and its building blocks, comments stripped): the key under which
+    a committed ncu summary is valid.  Host code is not part of it."""
     h = hashlib.sha256()
-    for f in ("paper_2209_08764_gb300/csrc/level_loop.cuh", "paper_2209_08764_gb300/csrc/s3bfs_device.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
             h.update(strip_c_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
-def profiled(workload, key="dram_bytes_per_launch"):
-    """A per-launch counter of the level-loop kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"level_loop_{workload}.json")
+def profiled(workload, key="dram_bytes_per_launch", name="level_loop", kernel="level_loop"):
+    """A per-launch counter from the committed ncu summary
+    profiles/<name>_<workload>.json, if it was taken on the current kernel
+    source; else None."""
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
     try:
         with open(path) as f:
             p = json.load(f)
     except (OSError, ValueError):
         return None
-    if p.get("kernel_source_sha256_16") != kernel_source_hash():
+    if p.get("kernel_source_sha256_16") != kernel_source_hash(kernel):
         return None
     return p.get(key)
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per launch of the level-loop kernel (ncu), or None."""
-    return profiled(workload, "dram_bytes_per_launch")
+def profiled_traffic(workload, name="level_loop", kernel="level_loop"):
+    """DRAM bytes per launch of a kernel (ncu), or None."""
+    return profiled(workload, "dram_bytes_per_launch", name, kernel)
 
 
 def gather_peak(torch, dev):
@@ -481,7 +488,9 @@ def measure_batch(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replicas
                 "config": dict(config_of(args.workload, w, rp, ci), mode="batch-bitmask", k=k,
                                parents=not args.no_parents),
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                             "frac": round(achieved / peak, 4),
+                             "traffic": profiled_traffic(args.workload, "msbfs", "msbfs") if P is not None else None,
+                             "peak_kind": peak_kind,
                              "kernel": "k_msbfs", "algorithmic_bytes_per_launch": bytes_launch,
                              "avg_launch_ms": kms, "model": "12 B per pulled edge + 24 B per vertex per level + 4 B (8 with parents) "
                                       "per (source, vertex) output"},
@@ -997,7 +1006,7 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     bytes_loop = np.tile(np.array(src_bytes, dtype=np.float64), args.steps)
     achieved = bytes_loop.sum() / (ms_loop.sum() / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic = profiled_traffic(args.workload) if not direction else None
+    traffic = profiled_traffic(args.workload, "direction_optimising" if direction else "level_loop")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "k_level_loop", "algorithmic_bytes_per_launch": float(bytes_loop.mean()),
