@@ -1299,15 +1299,29 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
 __device__ __forceinline__ void finalize_outputs(int32_t n, const int32_t* inv, const int32_t* perm,
                                                  const int32_t* level, const int32_t* parent, int32_t* level_out,
                                                  int32_t* parent_out) {
+  // four vertices a thread per step, their loads in flight together (the
+  // chain inv -> level, parent -> perm is latency-bound)
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-    const int i = __ldg(inv + v);
-    const int lv = level[i];
-    level_out[v] = lv;
-    if (parent_out) {
+  for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < n; v0 += 4 * stride) {
+    int i[4], lv[4], q[4], pp[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { const long long v = v0 + k * stride; i[k] = v < n ? __ldg(inv + v) : 0; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long v = v0 + k * stride;
+      lv[k] = v < n ? level[i[k]] : -1;
       // an unreached vertex's parent entry may never have been written
-      const int q = parent[i];
-      parent_out[v] = lv >= 0 ? __ldg(perm + q) : -1;
+      q[k] = (v < n && parent_out) ? parent[i[k]] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pp[k] = (lv[k] >= 0 && parent_out) ? __ldg(perm + q[k]) : -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long v = v0 + k * stride;
+      if (v < n) {
+        level_out[v] = lv[k];
+        if (parent_out) parent_out[v] = pp[k];
+      }
     }
   }
 }
