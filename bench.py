@@ -1051,10 +1051,16 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
         hp = torch.empty(len(S) * n, dtype=torch.int32, pin_memory=True)
         B.bfs_run_batch(g, S[:2], min(2, len(S)), hl, hp, None)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
+        # at least 16 calls, each timed: on some boxes an occasional call runs
+        # far longer than the rest, and the distribution shows it beside the mean
+        calls = max(args.steps, 16)
+        per_call = []
+        for _ in range(calls):
+            t0 = time.perf_counter()
             B.bfs_run_batch(g, S, len(S), hl, hp, None)
-        te = time.perf_counter() - t0
+            per_call.append(time.perf_counter() - t0)
+        te = sum(per_call)
+        med = float(np.median(per_call))
         # this box's plain device -> pinned host copy rate (one traversal's
         # level array, 8 times), beside which the end-to-end number is read
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1064,7 +1070,12 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
         e1.record()
         torch.cuda.synchronize()
         d2h_gbs = 8 * 4 * n / (e0.elapsed_time(e1) / 1e3) / 1e9
-        e2e = {"value": edges_per_step * args.steps / te / 1e9, "unit": "GTEPS",
+        e2e = {"value": edges_per_step * calls / te / 1e9, "unit": "GTEPS",
+               "calls": calls,
+               "ms_per_call": {"mean": round(te / calls * 1e3, 2), "median": round(med * 1e3, 2),
+                               "max": round(max(per_call) * 1e3, 2),
+                               "slow_calls": int(sum(t > 1.2 * med for t in per_call))},
+               "value_at_median_call": round(edges_per_step / med / 1e9, 3),
                "d2h_copy_gbs": round(d2h_gbs, 1), "cpu_affinity": getattr(args, "cpu_affinity", None),
                "h2d_bytes_per_step": 4 * len(srcs),
                "d2h_bytes_per_step": int(len(srcs) * (8 * n + ctypes.sizeof(ctypes.c_int64) * 8))}

@@ -53,7 +53,8 @@ struct bfs_graph {
   int32_t *d_arrive = nullptr, *d_smid = nullptr;
   DevState* d_st = nullptr;
   int32_t* d_lvl = nullptr;
-  DevState* h_st = nullptr;  // pinned
+  DevState* h_st = nullptr;      // pinned
+  DevState* h_st_map = nullptr;  // the device's pointer to h_st, if mapped
   int32_t* h_smid = nullptr; // pinned
   int32_t* h_ctrl = nullptr; // pinned, launch-per-phase mode
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -87,7 +88,8 @@ struct bfs_graph {
   int32_t *d_slot_level[2] = {nullptr, nullptr}, *d_slot_parent[2] = {nullptr, nullptr};
   cudaEvent_t slot_ev[kQueueDepth][3] = {};
   cudaEvent_t slot_ready[kQueueDepth] = {}, slot_copied[kQueueDepth] = {};
-  DevState* h_slot_st = nullptr;  // pinned [kQueueDepth]
+  DevState* h_slot_st = nullptr;      // pinned [kQueueDepth]
+  DevState* h_slot_st_map = nullptr;  // the device's pointer to h_slot_st, if mapped
 };
 
 // last error text of this host thread (bfs_last_error) and its setter

@@ -285,8 +285,16 @@ __global__ void k_check_csr(int32_t n, int32_t nnz, const int32_t* rp, const int
 
 // Outputs of a renumbered graph back in the caller's vertex ids: v is the
 // caller's id, inv[v] the internal one, perm[i] the caller's id of internal i.
+// With st_host set (a device-mapped pointer to pinned host memory), block 0
+// also copies the finished traversal's state block there, so no copy-engine
+// transfer has to sit between this kernel and the next traversal's.
 __global__ void __launch_bounds__(kThreads) k_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
                                                        const int32_t* level, const int32_t* parent,
-                                                       int32_t* level_out, int32_t* parent_out) {
+                                                       int32_t* level_out, int32_t* parent_out,
+                                                       const DevState* st, DevState* st_host) {
+  static_assert(sizeof(DevState) % sizeof(int32_t) == 0, "state block is copied in words");
+  if (st_host && blockIdx.x == 0)
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int32_t)); w += blockDim.x)
+      reinterpret_cast<int32_t*>(st_host)[w] = reinterpret_cast<const int32_t*>(st)[w];
   finalize_outputs(n, inv, perm, level, parent, level_out, parent_out);
 }

@@ -336,11 +336,17 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
   if ((rc = dalloc(g, &g->d_lvl, (size_t)g->lvl_cap * kLevelFields)) != BFS_OK) return rc;
   CUDA_TRY(cudaMemsetAsync(g->d_status, 0, sizeof(ChunkStatus) * (size_t)max_chunks, g->stream));
   CUDA_TRY(cudaMemsetAsync(g->d_st, 0, sizeof(DevState), g->stream));
-  if (cudaHostAlloc((void**)&g->h_st, sizeof(DevState), cudaHostAllocDefault) != cudaSuccess ||
+  if (cudaHostAlloc((void**)&g->h_st, sizeof(DevState), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostAlloc((void**)&g->h_smid, sizeof(int32_t) * (size_t)g->ctas, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void**)&g->h_ctrl, sizeof(LevelCtrl) * 2 + 16, cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     return fail(BFS_E_NOMEM, "pinned host allocation failed");
+  }
+  // k_finalize writes a renumbered graph's state block through the device's
+  // view of h_st; without one it is copied after the kernel instead
+  if (cudaHostGetDevicePointer((void**)&g->h_st_map, g->h_st, 0) != cudaSuccess) {
+    cudaGetLastError();
+    g->h_st_map = nullptr;
   }
   for (auto& e : g->ev) CUDA_TRY(cudaEventCreate(&e));
 
@@ -542,8 +548,10 @@ static int traversal_stats(const bfs_graph* g, const DevState& st, int launches,
   return BFS_OK;
 }
 
-static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t src) {
-  CUDA_TRY(cudaMemcpyAsync(g->h_st, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+// state_on_host: k_finalize already wrote the state block into h_st
+static int finish_traversal(bfs_graph* g, bfs_stats* stats, bool timed, int32_t src, bool state_on_host) {
+  if (!state_on_host)
+    CUDA_TRY(cudaMemcpyAsync(g->h_st, g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
   if (stats && g->persistent)
     CUDA_TRY(cudaMemcpyAsync(g->h_smid, g->d_smid, sizeof(int32_t) * (size_t)g->ctas, cudaMemcpyDeviceToHost,
                              g->stream));
@@ -598,7 +606,8 @@ static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* paren
     int32_t* lo = lvl_dev ? level_out : g->d_out_level;
     int32_t* po = parent_out ? (par_dev ? parent_out : g->d_out_parent) : nullptr;
     const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
-    k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, level, parent, lo, po);
+    k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, level, parent, lo, po, g->d_st,
+                                                  g->h_st_map);
     CUDA_TRY(cudaGetLastError());
     ++g->launches;
     lvl_src = lo;
@@ -609,7 +618,7 @@ static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* paren
   if (parent_out && !par_dev)
     CUDA_TRY(cudaMemcpyAsync(parent_out, par_src, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost,
                              g->stream));
-  return finish_traversal(g, stats, timed, src);
+  return finish_traversal(g, stats, timed, src, g->relabel && g->h_st_map);
 }
 
 extern "C" int bfs_run(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* parent_out, bfs_stats* stats) {
@@ -868,11 +877,17 @@ static int pipe_setup(bfs_graph* g, bool host) {
   }
   if (!g->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
   if (!g->h_slot_st &&
-      cudaHostAlloc((void**)&g->h_slot_st, bfs_graph::kQueueDepth * sizeof(DevState), cudaHostAllocDefault) !=
+      cudaHostAlloc((void**)&g->h_slot_st, bfs_graph::kQueueDepth * sizeof(DevState), cudaHostAllocMapped) !=
           cudaSuccess) {
     cudaGetLastError();
     g->h_slot_st = nullptr;
     return fail(BFS_E_NOMEM, "pinned host allocation failed");
+  }
+  // k_finalize writes the state blocks through the device's view of them;
+  // without one (no mapped pinned memory) they are copied after it instead
+  if (!g->h_slot_st_map && cudaHostGetDevicePointer((void**)&g->h_slot_st_map, g->h_slot_st, 0) != cudaSuccess) {
+    cudaGetLastError();
+    g->h_slot_st_map = nullptr;
   }
   g->pipe_ready = true;
   return BFS_OK;
@@ -920,12 +935,14 @@ static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int
     }
     if (g->relabel) {
       const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
-      k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, lw, pw, lo, po);
+      k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, lw, pw, lo, po, g->d_st,
+                                                    g->h_slot_st_map ? g->h_slot_st_map + s : nullptr);
       CUDA_TRY(cudaGetLastError());
       ++g->launches;
     }
     launches[s] = g->launches;
-    CUDA_TRY(cudaMemcpyAsync(&g->h_slot_st[s], g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+    if (!g->relabel || !g->h_slot_st_map)
+      CUDA_TRY(cudaMemcpyAsync(&g->h_slot_st[s], g->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
     CUDA_TRY(cudaEventRecord(g->slot_ready[s], g->stream));
     if (host) {
       CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, g->slot_ready[s], 0));
