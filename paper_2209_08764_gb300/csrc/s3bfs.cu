@@ -400,6 +400,9 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.parent = parent;
   // a renumbered graph's outputs always pass through k_finalize
   p.parent_lazy = g->relabel ? 1 : 0;
+  // graphs renumbered by degree are the skewed ones, where a proportional
+  // guess of the start entry misses
+  p.guess_search = g->relabel ? 0 : 1;
   for (int b = 0; b < 2; ++b) {
     p.F[b] = g->d_F[b];
     p.RS[b] = g->d_RS[b];

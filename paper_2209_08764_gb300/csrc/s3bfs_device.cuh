@@ -152,6 +152,10 @@ struct Params {
   int32_t direction;  // 0: every level top-down; 1: direction-optimising
   int32_t alpha, beta, gamma;
   int32_t n_live;     // vertices of degree > 0 (the ones a bottom-up level can find)
+  // 1: the start-point search first probes the entries around
+  // e_begin * n_l / e_l (graphs of near-uniform degree, where EX is close to
+  // linear in the entry index); 0: plain 32-ary search (skewed graphs)
+  int32_t guess_search;
 #if S3BFS_CHECKED
   // checked build: every frontier in level order (F_0, F_1, ...), n entries
   // (null: no dump)
@@ -501,6 +505,29 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
   // lanes probe 32 evenly spaced entries of [lo, hi) and keep the last probe
   // that is still <= e_begin.  Invariant: EX[lo] <= e_begin < EX[hi].
   int lo = 0, hi = n_l;
+  if (p.guess_search && n_l > kWarp) {
+    // one round around the proportional guess first: 32 consecutive entries
+    // (every 32nd entry on a level of more than kGuessWide entries).  The
+    // probes only shrink [lo, hi) and keep the invariant; on a near-uniform
+    // degree they bracket the start, which leaves one step (or none).
+    constexpr int kGuessWide = 8192;
+    const int s = n_l > kGuessWide ? kWarp : 1;
+    const long long g0 = (long long)e_begin * n_l / e_l - (long long)(kWarp / 2) * s;
+    const long long x = min(max(g0 + (long long)lane * s, 0ll), (long long)n_l - 1);
+    // positions never decrease with the lane, so the probes <= e_begin are a prefix
+    const int c = __popc(__ballot_sync(kFull, in_range(p, x, n_l + 1, 10) && ld_cg(EX + x) <= e_begin));
+    const int x_first = __shfl_sync(kFull, (int)x, 0);
+    const int x_le = __shfl_sync(kFull, (int)x, max(c - 1, 0));
+    const int x_gt = __shfl_sync(kFull, (int)x, min(c, kWarp - 1));
+    if (c == 0) {
+      hi = x_first;  // > 0: EX[0] = 0 <= e_begin
+    } else if (c == kWarp) {
+      lo = x_le;
+    } else {
+      lo = x_le;
+      hi = x_gt;
+    }
+  }
   while (hi - lo > 1) {
     // S3BFS_PPL probes per lane a round (lane L probes PPL*L .. PPL*L + PPL - 1)
     constexpr int kPpl = S3BFS_PPL;
@@ -522,17 +549,38 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
   int i = lo;  // current frontier entry
   int e = e_begin;
   int cnt = 0;
-  while (e < e_end) {
-    // Stage a window of 32 frontier entries, one per lane: its first edge
-    // EX[idx], the edge after its last EX[idx+1], its row start and vertex.
+  // A window of 32 frontier entries, one per lane: its first edge EX[idx],
+  // the edge after its last EX[idx+1], its row start and vertex.  The next
+  // window's loads are issued as soon as its start is known (right after the
+  // current window is staged), so they run under the current window's walk.
+  bool pf_in;
+  int pf_lo, pf_hi, pf_rs, pf_u;
+  {
     const int idx = i + lane;
-    const bool in = idx < n_l && in_range(p, n_l, (long long)p.n + 1, 11) && in_range(p, idx, p.n, 12);
-    const int ex_lo = in ? ld_cg(EX + idx) : e_l;
+    pf_in = idx < n_l && in_range(p, n_l, (long long)p.n + 1, 11) && in_range(p, idx, p.n, 12);
+    pf_lo = pf_in ? ld_cg(EX + idx) : e_l;
+    pf_hi = (pf_in && lane == kWarp - 1) ? ld_cg(EX + idx + 1) : e_l;
+    pf_rs = pf_in ? ld_cg(RS + idx) : 0;
+    pf_u = pf_in ? ld_cg(F + idx) : 0;
+  }
+  while (e < e_end) {
+    const bool in = pf_in;
+    const int ex_lo = pf_lo;
     int ex_hi = __shfl_down_sync(kFull, ex_lo, 1);
-    if (lane == kWarp - 1) ex_hi = in ? ld_cg(EX + idx + 1) : e_l;
-    const int rs = in ? ld_cg(RS + idx) : 0;
-    const int u = in ? ld_cg(F + idx) : 0;
+    if (lane == kWarp - 1) ex_hi = pf_hi;
+    const int rs = pf_rs;
+    const int u = pf_u;
     const int tile_end = min(e_end, __shfl_sync(kFull, ex_hi, kWarp - 1));
+    // the next window starts past the entries whose edges this one finishes
+    const int i_next = i + __popc(__ballot_sync(kFull, in && ex_hi <= tile_end));
+    if (tile_end < e_end) {
+      const int idx = i_next + lane;
+      pf_in = idx < n_l && in_range(p, idx, p.n, 12);
+      pf_lo = pf_in ? ld_cg(EX + idx) : e_l;
+      pf_hi = (pf_in && lane == kWarp - 1) ? ld_cg(EX + idx + 1) : e_l;
+      pf_rs = pf_in ? ld_cg(RS + idx) : 0;
+      pf_u = pf_in ? ld_cg(F + idx) : 0;
+    }
     // This lane's edges inside the tile, as CSR positions [p0, p1), covered by
     // the 16-byte aligned quads q0 .. q0+nq-1 of col_idx.
     const int a = max(ex_lo, e), b = min(ex_hi, tile_end);
@@ -629,8 +677,7 @@ __device__ S3BFS_EXPLORE_QUAL int explore_chunk(const Params& p, int l, int par,
         }
       }
     }
-    // advance past the entries whose edges are all done
-    i += __popc(__ballot_sync(kFull, in && ex_hi <= tile_end));
+    i = i_next;
     e = tile_end;
   }
   return cnt;

@@ -380,6 +380,7 @@ static int admit(bfs_server* s) {
     p.grain = s->grain;
     p.work_insensitive = 0;
     p.src = g->relabel ? g->h_inv[(size_t)q.src] : q.src;
+    p.guess_search = g->relabel ? 0 : 1;
     p.max_chunks = s->ctas;
     p.debug_flags = 0;
     p.spin_ns = s->spin_ns;
