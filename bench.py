@@ -988,8 +988,12 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     recs = []
     with ClockSampler(dev) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
-            recs += step(True)
+        # the last step records every traversal's CUDA events (its launches
+        # give the per-launch durations); the others run without them, as a
+        # caller that wants only throughput does (the events cost ~5 us a
+        # traversal)
+        for k in range(args.steps):
+            recs += step(True if k == args.steps - 1 else None)
         ev1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -1002,8 +1006,9 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
     # roofline of the dominant kernel (the persistent level loop): algorithmic
     # bytes of each traversal's level loop / its device time
     recs = np.array(recs, dtype=np.float64)
+    rec_steps = len(recs) // len(S)  # steps whose launches were timed
     ms_loop = recs[:, 0]
-    bytes_loop = np.tile(np.array(src_bytes, dtype=np.float64), args.steps)
+    bytes_loop = np.tile(np.array(src_bytes, dtype=np.float64), rec_steps)
     achieved = bytes_loop.sum() / (ms_loop.sum() / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = profiled_traffic(args.workload, "direction_optimising" if direction else "level_loop")
@@ -1020,8 +1025,9 @@ def measure_single(args, w, rp, ci, srcs, B, torch, dist, ws, rank, dev, replica
                                        "unit": "sectors/s", "frac": round(ach / peak_ld, 4),
                                        "sectors_per_launch": sectors,
                                        "peak_kind": "measured: torch index_select of random int32"}
-    hmean = len(ms_loop) / np.sum(ms_loop / 1e3 / np.tile(teps_edges, args.steps)) / 1e9
-    launches = int(recs[:, 7].sum())
+    hmean = len(ms_loop) / np.sum(ms_loop / 1e3 / np.tile(teps_edges, rec_steps)) / 1e9
+    # launches per traversal are the same in every step
+    launches = int(recs[:, 7].sum()) * args.steps // rec_steps
     energy = None
     if not args.no_energy and rank == 0:
         energy = energy_per_traversal(EnergyMeter(torch, dev), lambda s: B.bfs_run(g, s, level, parent, None), srcs)
