@@ -213,11 +213,10 @@ int bfs_run(bfs_graph *g, int32_t src, int32_t *level_out, int32_t *parent_out, 
  * sources run one after another.  With the persistent loop, no per-level
  * records requested and both outputs on the same side (device or host), the
  * traversals are queued back to back, up to 8 ahead of the host, which
- * checks each one as it finishes.  Host outputs then go through two device
- * staging slots
- * (2 x n int32 each, allocated at the first such call) and a second stream
- * copies traversal i's outputs while traversal i + 1 runs, so pinned host
- * buffers cost little beyond the traversals themselves.
+ * checks each one as it finishes.  Host outputs then go through eight device
+ * staging slots (2 x n int32 each, allocated at the first such call) and a
+ * second stream copies traversal i's outputs while the next traversals run,
+ * so pinned host buffers cost little beyond the traversals themselves.
  *
  * Errors as for bfs_run; on error the index of the failing source (or group)
  * is in bfs_last_error().

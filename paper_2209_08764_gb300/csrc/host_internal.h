@@ -80,12 +80,13 @@ struct bfs_graph {
   int32_t *d_stage_level = nullptr, *d_stage_parent = nullptr;  // 64 x n, for host outputs
   // batches of single-source traversals queued back to back: a ring of
   // kQueueDepth slots (events, pinned state block) lets the host run that many
-  // traversals ahead; with host outputs also two device staging pairs (level,
-  // parent) whose copies to the host overlap the next traversal
+  // traversals ahead; with host outputs also one device staging pair (level,
+  // parent) per slot, whose copy to the host overlaps the traversals after it
   static constexpr int kQueueDepth = 8;
+  static constexpr int kStagePairs = kQueueDepth;
   bool pipe_ready = false;
   cudaStream_t copy_stream = nullptr;
-  int32_t *d_slot_level[2] = {nullptr, nullptr}, *d_slot_parent[2] = {nullptr, nullptr};
+  int32_t *d_slot_level[kStagePairs] = {}, *d_slot_parent[kStagePairs] = {};
   cudaEvent_t slot_ev[kQueueDepth][3] = {};
   cudaEvent_t slot_ready[kQueueDepth] = {}, slot_copied[kQueueDepth] = {};
   DevState* h_slot_st = nullptr;      // pinned [kQueueDepth]

@@ -857,19 +857,21 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
 // and checks traversal i - D (error, stats) before it reuses that slot, so a
 // host that falls behind for a while does not leave the GPU idle.  Device
 // outputs are written in place (through k_finalize on a renumbered graph).
-// Host outputs go through device staging pair i & 1: a second stream copies
-// it to the caller's buffers while traversal i + 1 runs, and traversal i + 2
-// waits for that copy on the device before it reuses the pair.  Copies into
-// pageable host memory are correct but do not overlap.
+// Host outputs go through device staging pair i % S (S = kStagePairs): a
+// second stream copies it to the caller's buffers while the next traversals
+// run, and traversal i + S waits for that copy on the device before it
+// reuses the pair.  With S pairs the traversals can run S - 1 ahead of the
+// copies, so a copy that is slow for a while (the device-to-host path is
+// shared) delays no traversal as long as the copies keep up on average.
+// Copies into pageable host memory are correct but do not overlap.
 
 static int pipe_setup(bfs_graph* g, bool host) {
   int rc;
-  if (host && !g->d_slot_level[1]) {
-    for (int s = 0; s < 2; ++s) {
-      if ((rc = dalloc(g, &g->d_slot_level[s], (size_t)g->n + 4)) != BFS_OK) return rc;
-      if ((rc = dalloc(g, &g->d_slot_parent[s], (size_t)g->n + 4)) != BFS_OK) return rc;
+  if (host)
+    for (int s = 0; s < bfs_graph::kStagePairs; ++s) {
+      if (!g->d_slot_level[s] && (rc = dalloc(g, &g->d_slot_level[s], (size_t)g->n + 4)) != BFS_OK) return rc;
+      if (!g->d_slot_parent[s] && (rc = dalloc(g, &g->d_slot_parent[s], (size_t)g->n + 4)) != BFS_OK) return rc;
     }
-  }
   if (g->pipe_ready) return BFS_OK;
   // each handle is created once (a call that failed half-way resumes here)
   for (int s = 0; s < bfs_graph::kQueueDepth; ++s) {
@@ -922,8 +924,9 @@ static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int
       }
       ++done;
     }
-    const int s = i % D, b = i & 1;
-    if (host && i >= 2) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[(i - 2) % D], 0));
+    constexpr int S = bfs_graph::kStagePairs;
+    const int s = i % D, b = i % S;
+    if (host && i >= S) CUDA_TRY(cudaStreamWaitEvent(g->stream, g->slot_copied[(i - S) % D], 0));
     // this traversal's outputs on the device, and its working arrays
     int32_t* lo = host ? g->d_slot_level[b] : levels_out + (size_t)i * n;
     int32_t* po = parents_out ? (host ? g->d_slot_parent[b] : parents_out + (size_t)i * n) : nullptr;
