@@ -51,6 +51,11 @@ struct MsParams {
   int32_t* bar_arrive;
   long long spin_ns;
   int32_t debug_flags;
+  // 1: the outputs were not cleared; the kernel ends by writing -1 to every
+  // (source, vertex) pair it did not reach (each entry written once).  0: the
+  // host cleared them to -1 first (graphs with many isolated vertices, where
+  // writing the missing pairs piecemeal costs more than one clearing pass)
+  int32_t write_missing;
 };
 
 __device__ __forceinline__ unsigned long long ld_cg64(const unsigned long long* p) {
@@ -113,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
   const int* rp = p.row_ptr;
   const int* ci = p.col_idx;
   int l = 0, bar = 0;
+  bool finished = false;  // the loop ended with no source advancing (not on an error)
   // sources with a non-empty frontier at this level: the only bits a vertex
   // can gain now.  A vertex stops pulling once it holds all of them (and
   // skips its row when it already did), the early exit of multi-source BFS.
@@ -280,11 +286,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_msbfs(MsParams p) {
     __syncthreads();
     const unsigned long long any = s_any;
     __syncthreads();
-    if (any == 0) break;
+    if (any == 0) {
+      finished = true;
+      break;
+    }
     active = any;  // the sources whose frontier the next level pulls
     ++l;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) p.st->num_levels = l + 1;
+  if (finished && p.write_missing) {
+    // every (source, vertex) pair the sources never reached gets -1, so each
+    // output entry is written exactly once (no clearing pass beforehand).
+    // seen[] is final: the last grid barrier orders every CTA's writes.  A
+    // warp takes 32 consecutive caller ids; per source missing anywhere in
+    // the warp, one store per array for the lanes that miss it.
+    for (long long V0 = tid - lane; V0 < p.n; V0 += nthreads) {
+      const long long V = V0 + lane;
+      const long long v = V < p.n ? (p.inv ? __ldg(p.inv + V) : V) : 0;
+      const unsigned long long miss = V < p.n ? full & ~ld_cg64(p.seen + v) : 0ull;
+      unsigned long long wm = warp_or64(miss);
+      while (wm) {
+        const int i = __ffsll((long long)wm) - 1;
+        wm &= wm - 1;
+        if ((miss >> i) & 1ull) {
+          p.levels_out[(long long)i * p.n + V] = -1;
+          if (p.parents_out) p.parents_out[(long long)i * p.n + V] = -1;
+        }
+      }
+    }
+  }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) my_edges += __shfl_xor_sync(kFull, my_edges, o);
   if (lane == 0) s_edges[wib] = my_edges;

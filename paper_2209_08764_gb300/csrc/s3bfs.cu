@@ -250,8 +250,9 @@ static int create_impl(bfs_graph* g, int32_t n, int32_t nnz, const int32_t* row_
     }
   }
   const bool upload_from_host = csr_on_host;
-  if (g->direction) {
-    // vertices of degree > 0: the ones a bottom-up level can find
+  if (g->direction || g->symmetric) {
+    // vertices of degree > 0: the ones a bottom-up level can find (and, on a
+    // symmetric graph, the count that decides how a bitmask batch writes -1)
     std::vector<int32_t> rp_copy;
     const int32_t* rpp = rp;
     if (!csr_on_host) {
@@ -784,8 +785,16 @@ static int run_group_bitmask(bfs_graph* g, const int32_t* srcs, int k, int32_t* 
   p.debug_flags = 0;
   const bool timed = stats != nullptr;
   if (timed) CUDA_TRY(cudaEventRecord(g->ev[0], g->stream));
-  CUDA_TRY(cudaMemsetAsync(L, 0xFF, sizeof(int32_t) * (size_t)k * n, g->stream));
-  if (Pp) CUDA_TRY(cudaMemsetAsync(Pp, 0xFF, sizeof(int32_t) * (size_t)k * n, g->stream));
+  // With few isolated vertices k_msbfs writes every output entry once (-1 for
+  // the pairs it never reached); otherwise the outputs are cleared first.  On
+  // ER 2^20 the first saves the 83 us clearing pass of a 1.34 ms batch; on
+  // R-MAT s22 (43% of the vertices isolated) writing the missing pairs after
+  // the pull cost 0.75 ms against 0.54 ms for the clearing pass.
+  p.write_missing = (long long)(g->n - g->n_live) * 16 <= (long long)g->n ? 1 : 0;
+  if (!p.write_missing) {
+    CUDA_TRY(cudaMemsetAsync(L, 0xFF, sizeof(int32_t) * (size_t)k * n, g->stream));
+    if (Pp) CUDA_TRY(cudaMemsetAsync(Pp, 0xFF, sizeof(int32_t) * (size_t)k * n, g->stream));
+  }
   CUDA_TRY(cudaMemsetAsync(g->d_arrive, 0, sizeof(int32_t) * ((size_t)(g->ms_ctas + 3) / 4 * 4), g->stream));
   const int cgrid = std::max(1, std::min(g->sms * 8, (int)((n + kThreads - 1) / kThreads)));
   k_msbfs_clear<<<cgrid, kThreads, 0, g->stream>>>(p);

@@ -517,6 +517,52 @@ def test_batch_bitmask_er_and_grid():
         _batch_check(rp, ci, srcs, B.BFS_VALIDATE | B.BFS_SYMMETRIC)
 
 
+@pytest.mark.parametrize("k", [5, 64])
+@pytest.mark.parametrize("where", ["device", "host"])
+@pytest.mark.parametrize("parents", [True, False])
+def test_batch_bitmask_unreached_pairs_written(k, where, parents):
+    """A graph with few isolated vertices (here about 1%), whose bitmask
+    traversal writes -1 to the (source, vertex) pairs it never reached at the
+    end instead of clearing the outputs first: an ER part, a separate path and
+    isolated vertices, sources in all three.  Outputs start as a sentinel, so
+    an entry left unwritten fails; every row must equal the oracle's levels
+    and form a BFS tree."""
+    import torch
+    rp0, ci0 = graphgen.erdos_renyi(1 << 12, 1 << 14, seed=8)
+    n0 = len(rp0) - 1
+    rows = np.repeat(np.arange(n0), np.diff(rp0))
+    edges = [(int(a), int(b)) for a, b in zip(rows, ci0) if a < b]
+    n_path, n_iso = 60, 40
+    edges += [(n0 + j, n0 + j + 1) for j in range(n_path - 1)]
+    n = n0 + n_path + n_iso
+    rp, ci = graphgen.from_edges(n, edges)
+    assert (np.diff(rp) == 0).sum() * 16 <= n  # few isolated vertices: the end pass writes the misses
+    srcs = list(graphgen.sample_sources(rp0, k - 3, seed=5)) + [n0 + 7, n0 + n_path - 1, n - 1]
+    S = np.ascontiguousarray(srcs, np.int32)
+    g = B.bfs_create_csr(n, len(ci), rp, ci, B.BFS_VALIDATE | B.BFS_SYMMETRIC, None,
+                         torch.cuda.current_stream().cuda_stream)
+    try:
+        if where == "host":
+            L = np.full(k * n, 12345, np.int32)
+            P = np.full(k * n, 12345, np.int32) if parents else None
+        else:
+            L = torch.full((k * n,), 12345, dtype=torch.int32, device="cuda")
+            P = torch.full((k * n,), 12345, dtype=torch.int32, device="cuda") if parents else None
+        for _ in range(2):  # the second call reuses the staging buffers the first one filled
+            B.bfs_run_batch(g, S, k, L, P, None)
+        Lh = (L if where == "host" else L.cpu().numpy()).reshape(k, n)
+        orc = oracle.Oracle(rp, ci)
+        keys = oracle.edge_keys(rp, ci)
+        for i, s in enumerate(S):
+            want, _ = orc.bfs(int(s))
+            assert np.array_equal(Lh[i], want), f"source {i} ({s}): levels differ"
+            if parents:
+                Ph = (P if where == "host" else P.cpu().numpy()).reshape(k, n)
+                oracle.check_bfs_tree(rp, ci, int(s), Lh[i], Ph[i], keys=keys)
+    finally:
+        B.bfs_destroy(g)
+
+
 def test_batch_bitmask_off_and_asymmetric_rejected():
     rp, ci = graphgen.rmat(12, 16, seed=3)
     srcs = graphgen.sample_sources(rp, 8, seed=2)
