@@ -127,7 +127,7 @@ __device__ __noinline__ bool bu_level(const Params& p, int l, int n_l, int e_l, 
   }
 #endif
   // warp gw's region: 128 entries per 128-vertex group it owns
-  const int gpw = ((p.nwords >> 2) + P - 1) / P;
+  const int gpw = (p.bu_groups + P - 1) / P;
   const long long base = (long long)gw * gpw * 128;
   int work = 0, first = 0, work0 = 0;
   const int total = after_bu ? ld_relaxed(p.ulist_cnt + gw)

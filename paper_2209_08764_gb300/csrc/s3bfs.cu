@@ -430,6 +430,8 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.fb[0] = g->d_fb[0];
   p.fb[1] = g->d_fb[1];
   p.nwords = g->nwords;
+  // degree-descending renumbering puts the n - n_live isolated vertices last
+  p.bu_groups = g->relabel ? (int32_t)(((long long)g->n_live + 127) / 128) : g->nwords / 4;
   p.ulist = g->d_ulist;
   p.ulist_cnt = g->d_ulist_cnt;
   p.direction = g->persistent ? g->direction : 0;

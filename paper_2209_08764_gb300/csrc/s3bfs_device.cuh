@@ -145,6 +145,11 @@ struct Params {
   // level[v] == l) and write the next level's bitmap fb[(l + 1) & 1]
   uint32_t* fb[2];
   int32_t nwords;     // words of a frontier bitmap: ceil(n / 32), padded to a multiple of 4
+  // 128-vertex groups a bottom-up level scans for unvisited vertices: all
+  // (nwords / 4), or on a graph renumbered by descending degree only those up
+  // to the last vertex of degree > 0 (the isolated ones come last and no
+  // level ever reaches them)
+  int32_t bu_groups;
   // per warp: the vertices still unvisited after a bottom-up level (in the
   // warp's region, like its candidates) and their count
   int32_t* ulist;
@@ -1156,7 +1161,7 @@ __device__ inline int bu_unvisited(const Params& p, int l, const uint32_t* fb, i
   const int lane = threadIdx.x & (kWarp - 1);
   const unsigned lt = (1u << lane) - 1u;
   int cnt = 0, nf = 0, wk = 0;
-  for (int q = gw; q < (p.nwords >> 2); q += P) {
+  for (int q = gw; q < p.bu_groups; q += P) {
     int lv[4], rs[4], re[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
