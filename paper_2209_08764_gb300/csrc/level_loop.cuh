@@ -291,10 +291,11 @@ __global__ void k_check_csr(int32_t n, int32_t nnz, const int32_t* rp, const int
 __global__ void __launch_bounds__(kThreads) k_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
                                                        const int32_t* level, const int32_t* parent,
                                                        int32_t* level_out, int32_t* parent_out,
-                                                       const DevState* st, DevState* st_host) {
+                                                       const DevState* st, DevState* st_host, int32_t n_kept,
+                                                       int32_t s) {
   static_assert(sizeof(DevState) % sizeof(int32_t) == 0, "state block is copied in words");
   if (st_host && blockIdx.x == 0)
     for (int w = threadIdx.x; w < (int)(sizeof(DevState) / sizeof(int32_t)); w += blockDim.x)
       reinterpret_cast<int32_t*>(st_host)[w] = reinterpret_cast<const int32_t*>(st)[w];
-  finalize_outputs(n, inv, perm, level, parent, level_out, parent_out);
+  finalize_outputs(n, inv, perm, level, parent, level_out, parent_out, n_kept, s);
 }

@@ -430,8 +430,12 @@ static Params make_params(bfs_graph* g, int32_t src, int32_t* level, int32_t* pa
   p.fb[0] = g->d_fb[0];
   p.fb[1] = g->d_fb[1];
   p.nwords = g->nwords;
-  // degree-descending renumbering puts the n - n_live isolated vertices last
-  p.bu_groups = g->relabel ? (int32_t)(((long long)g->n_live + 127) / 128) : g->nwords / 4;
+  // degree-descending renumbering puts the vertices of degree 0 last; on a
+  // symmetric graph those are the n - n_live isolated ones, which no level
+  // reaches (on a directed one a vertex without out-edges may be reached)
+  const bool isolated_last = g->relabel && g->symmetric && g->n_live > 0;
+  p.bu_groups = isolated_last ? (int32_t)(((long long)g->n_live + 127) / 128) : g->nwords / 4;
+  p.level_n = isolated_last ? g->n_live : g->n;
   p.ulist = g->d_ulist;
   p.ulist_cnt = g->d_ulist_cnt;
   p.direction = g->persistent ? g->direction : 0;
@@ -613,7 +617,7 @@ static int run_one(bfs_graph* g, int32_t src, int32_t* level_out, int32_t* paren
     int32_t* po = parent_out ? (par_dev ? parent_out : g->d_out_parent) : nullptr;
     const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
     k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, level, parent, lo, po, g->d_st,
-                                                  g->h_st_map);
+                                                  g->h_st_map, p.level_n, p.src);
     CUDA_TRY(cudaGetLastError());
     ++g->launches;
     lvl_src = lo;
@@ -953,7 +957,8 @@ static int run_batch_pipelined(bfs_graph* g, const int32_t* srcs, int32_t k, int
     if (g->relabel) {
       const int fgrid = std::max(1, std::min(g->sms * 8, (int)(((long long)g->n + kThreads - 1) / kThreads)));
       k_finalize<<<fgrid, kThreads, 0, g->stream>>>(g->n, g->d_inv, g->d_perm, lw, pw, lo, po, g->d_st,
-                                                    g->h_slot_st_map ? g->h_slot_st_map + s : nullptr);
+                                                    g->h_slot_st_map ? g->h_slot_st_map + s : nullptr, p.level_n,
+                                                    p.src);
       CUDA_TRY(cudaGetLastError());
       ++g->launches;
     }

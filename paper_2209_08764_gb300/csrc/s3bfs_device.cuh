@@ -150,6 +150,10 @@ struct Params {
   // to the last vertex of degree > 0 (the isolated ones come last and no
   // level ever reaches them)
   int32_t bu_groups;
+  // level entries a traversal clears and finalize_outputs reads: n, or on a
+  // graph renumbered by descending degree (parent_lazy) the vertices of
+  // degree > 0, which come first (no edge reaches the isolated ones; 0 = n)
+  int32_t level_n;
   // per warp: the vertices still unvisited after a bottom-up level (in the
   // warp's region, like its candidates) and their count
   int32_t* ulist;
@@ -1287,7 +1291,11 @@ __device__ __forceinline__ void record_level(const Params& p, int l, int n_l, in
 __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const int n = p.n, s = p.src;
+  const int s = p.src;
+  // entries to clear (parents are cleared only where they are not lazy, and
+  // there level_n is n)
+  const int n = (p.parent_lazy && p.level_n > 0 && p.level_n < p.n) ? p.level_n : p.n;
+  if (tid == 0 && s >= n) p.level[s] = 0;  // an isolated source past the cleared part
   const bool vec = ((reinterpret_cast<uintptr_t>(p.level) | reinterpret_cast<uintptr_t>(p.parent)) & 15) == 0;
   if (vec) {
     int4* L4 = reinterpret_cast<int4*>(p.level);
@@ -1348,9 +1356,11 @@ __device__ __forceinline__ void init_traversal(const Params& p, int ctas) {
   }
 }
 
+// Internal ids i >= n_kept are isolated vertices whose level entries the
+// traversal never touched: -1, except the source s (level 0, its own parent).
 __device__ __forceinline__ void finalize_outputs(int32_t n, const int32_t* inv, const int32_t* perm,
                                                  const int32_t* level, const int32_t* parent, int32_t* level_out,
-                                                 int32_t* parent_out) {
+                                                 int32_t* parent_out, int32_t n_kept, int32_t s) {
   // four vertices a thread per step, their loads in flight together (the
   // chain inv -> level, parent -> perm is latency-bound)
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1361,9 +1371,10 @@ __device__ __forceinline__ void finalize_outputs(int32_t n, const int32_t* inv, 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const long long v = v0 + k * stride;
-      lv[k] = v < n ? level[i[k]] : -1;
+      const bool kept = v < n && i[k] < n_kept;
+      lv[k] = kept ? level[i[k]] : (v < n && i[k] == s ? 0 : -1);
       // an unreached vertex's parent entry may never have been written
-      q[k] = (v < n && parent_out) ? parent[i[k]] : 0;
+      q[k] = (kept && parent_out) ? parent[i[k]] : i[k];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) pp[k] = (lv[k] >= 0 && parent_out) ? __ldg(perm + q[k]) : -1;

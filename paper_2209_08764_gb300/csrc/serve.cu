@@ -44,7 +44,7 @@ static const void* serve_fn(int wpc) {
 __global__ void __launch_bounds__(256) k_serve_finalize(int32_t n, const int32_t* inv, const int32_t* perm,
                                                         const int32_t* level, const int32_t* parent,
                                                         int32_t* level_out, int32_t* parent_out) {
-  finalize_outputs(n, inv, perm, level, parent, level_out, parent_out);
+  finalize_outputs(n, inv, perm, level, parent, level_out, parent_out, n, -1);  // the server clears every entry
 }
 
 namespace {

@@ -517,6 +517,40 @@ def test_batch_bitmask_er_and_grid():
         _batch_check(rp, ci, srcs, B.BFS_VALIDATE | B.BFS_SYMMETRIC)
 
 
+@pytest.mark.parametrize("direction", [0, 1])
+def test_isolated_vertices_on_renumbered_graph(direction):
+    """A symmetric graph renumbered by degree puts its isolated vertices last;
+    a traversal then clears and reads only the others' level entries.  Sources
+    that are isolated (level 0 alone, its own parent) and ordinary ones, in
+    single runs and in a queued batch, must equal the oracle, also after runs
+    that left the untouched tail alone."""
+    import torch
+    rp0, ci0 = graphgen.rmat(12, 8, seed=4)
+    n = len(rp0) - 1
+    deg = np.diff(rp0)
+    iso = np.nonzero(deg == 0)[0]
+    assert len(iso) > 10
+    d = Dev(rp0, ci0, flags=B.BFS_VALIDATE | B.BFS_SYMMETRIC, relabel=1, direction=direction, batch_bitmask=-1)
+    orc = oracle.Oracle(rp0, ci0)
+    try:
+        live = graphgen.sample_sources(rp0, 3, seed=9)
+        order = [int(iso[0]), int(live[0]), int(iso[-1]), int(live[1]), int(iso[len(iso) // 2]), int(live[2])]
+        for s in order:
+            check_against_oracle(d, s, orc=orc)
+        S = np.ascontiguousarray(order, np.int32)
+        L = torch.full((len(S) * n,), 77, dtype=torch.int32, device="cuda")
+        P = torch.full((len(S) * n,), 77, dtype=torch.int32, device="cuda")
+        B.bfs_run_batch(d.g, S, len(S), L, P, None)
+        L, P = L.cpu().numpy().reshape(len(S), n), P.cpu().numpy().reshape(len(S), n)
+        keys = oracle.edge_keys(rp0, ci0)
+        for i, s in enumerate(S):
+            want, _ = orc.bfs(int(s))
+            assert np.array_equal(L[i], want), f"source {s}"
+            oracle.check_bfs_tree(rp0, ci0, int(s), L[i], P[i], keys=keys)
+    finally:
+        d.close()
+
+
 @pytest.mark.parametrize("k", [5, 64])
 @pytest.mark.parametrize("where", ["device", "host"])
 @pytest.mark.parametrize("parents", [True, False])
