@@ -798,14 +798,15 @@ def arm_er20_batch(args, B, torch, dev, replicas, line):
     return out
 
 
-GRID_TUNE_SPACE = {"cta_warps": [0, 8, 32], "small_level_edges": [0, 8192], "chunk_edges": [0, 32]}
+GRID_TUNE_SPACE = {"cta_warps": [0, 8, 32], "small_level_edges": [0, 8192], "chunk_edges": [0, 32], "ctas": [0, -2]}
 
 
 def arm_grid4096(args, B, torch, dev, replicas):
     """4096^2 grid with 1% of edges deleted: the corner (deepest source) and 7
     seeded sources, single-source S3BFS with the default options and with the
     options the autotuner picks (coordinate descent over the CTA shape, the
-    small-level threshold and the grain, on the corner source).  Per level
+    small-level threshold, the grain and the grid size, on the corner
+    source).  Per level
     also in SM cycles (us x the median sampled SM MHz), which takes the box's
     clock out of the comparison."""
     from paper_2209_08764_gb300 import autotune

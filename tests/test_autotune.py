@@ -75,3 +75,13 @@ def test_skew_needs_a_large_graph():
     rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
     ci = np.zeros(int(rp[-1]), np.int32)
     assert autotune.graph_key(rp, ci).endswith("flat")
+
+
+def test_resolve_maps_grid_size_codes():
+    """ctas = -1 is one CTA per SM, -2 half the SMs (at least one); other
+    values pass through."""
+    from paper_2209_08764_gb300 import autotune
+    assert autotune.resolve({"ctas": -1}, 152)["ctas"] == 152
+    assert autotune.resolve({"ctas": -2}, 152)["ctas"] == 76
+    assert autotune.resolve({"ctas": -2}, 1)["ctas"] == 1
+    assert autotune.resolve({"ctas": 0, "chunk_edges": 32}, 152) == {"ctas": 0, "chunk_edges": 32}
